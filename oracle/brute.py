@@ -1,0 +1,38 @@
+"""NumPy brute force of the RI-MP2 energy and intermediates from the explicit 4-index
+integrals (ia|jb).  TEST INFRASTRUCTURE ONLY, for tiny sizes.
+
+It forms the whole (ia|jb) array (Eq. MP2_ints) and the amplitudes of the Appendix
+with einsum, independently of the C loops in rimp2_oracle.c, so the two check each
+other.  Definitions are the ones listed in that file's header.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def integrals(B):
+    """(ia|jb)_RI = sum_Q B^Q_ia B^Q_jb as an array [i, a, j, b]."""
+    return np.einsum("iaQ,jbQ->iajb", B, B)
+
+
+def denominators(eo, ev):
+    """D[i, a, j, b] = e_i + e_j - e_a - e_b."""
+    return (eo[:, None, None, None] + eo[None, None, :, None]
+            - ev[None, :, None, None] - ev[None, None, None, :])
+
+
+def everything(B, eo, ev):
+    """Dict with energy, gamma, pij, pab, epair (brute force)."""
+    iajb = integrals(B)
+    T = iajb / denominators(eo, ev)                 # X^ab_ij stored as T[i, a, j, b]
+    Tt = 2.0 * T - T.transpose(0, 3, 2, 1)          # 2 X^ab_ij - X^ba_ij
+    epair = np.einsum("iajb,iajb->ij", Tt, iajb)
+    energy = float(np.sum(epair))
+    gamma = np.einsum("iajb,jbQ->iaQ", Tt, B)
+    pij = -np.einsum("iakb,jakb->ij", Tt, T)
+    pab = np.einsum("iajc,ibjc->ab", Tt, T)
+    return {"energy": energy, "gamma": gamma, "pij": pij, "pab": pab, "epair": epair}
+
+
+def energy(B, eo, ev) -> float:
+    return everything(B, eo, ev)["energy"]
