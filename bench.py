@@ -1,0 +1,301 @@
+"""Benchmark of the RI-MP2 energy + gradient-intermediate hot path on one GB300.
+
+Workload: one large fragment, nocc=100, nvir=500, naux=1500 (seeded synthetic B and
+orbital energies), energy + Gamma + P_ij + P_ab per step.  A step is one full pass of
+the hot path.  Inputs (600 MB) and workspace (tens of GB) are far larger than L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision auto|fp64|bf16]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Under torchrun each rank runs its own replica (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RI-MP2 energy+grad TFLOP/s and fragments/s on 1 GB300, vs plain FP64 at <=1e-8 Eh"
+WORKLOAD = {"workload": "single fragment RI-MP2 energy+Gamma+P_ab+P_ij, nocc=100 nvir=500 "
+                        "naux=1500, seed 0", "nocc": 100, "nvir": 500, "naux": 1500}
+DIMS = (100, 500, 1500)
+
+
+def flops(o, v, X):
+    """2mnk count (V over i<=j, Gamma, P_ab, P_ij)."""
+    return float(o * (o + 1) * v * v * X + 2 * o * o * v * v * X + 2 * o * o * v ** 3
+                 + 2 * o ** 3 * v * v)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(B, eo, ev, max_seconds=25.0):
+    """The oracle, as it stands, on a bounded sample of the workload: a slice of the
+    second pair index k (each k is 1/nocc of the pairs), scaled to TFLOP/s."""
+    from oracle import oracle
+    o, v, X = B.shape
+    nthr = oracle.threads()
+    t0 = time.perf_counter()
+    k = 0
+    while k < o:
+        oracle.fragment(B, eo, ev, k_range=(k, k + 1), nthreads=nthr)
+        k += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    val = flops(o, v, X) * k / o / dt / 1e12
+    return {"value": val, "unit": "TFLOP/s", "cores": nthr, "kind": "oracle",
+            "sample": f"pairs (i,k) for k in [0,{k}) of nocc={o} nvir={v} naux={X} "
+                      f"(energy, Gamma, P_ij, P_ab contributions; {dt:.1f} s)",
+            "seconds": dt, "k_done": k}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2410_21888_gb300 import synth
+    o, v, X = DIMS
+    f = synth.fragment_inputs(o, v, X, seed=0)
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(f.B, f.eo, f.ev, max_seconds=2.0)
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(f.B, f.eo, f.ev, max_seconds=max(5.0, 60.0 / max(args.steps, 1)))
+        vals.append(cb["value"])
+    value = statistics.median(vals)
+    ms = flops(o, v, X) / (value * 1e12) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, l2="CPU run"),
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the plain FP64 path reported beside the split path")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_21888_gb300 import rimp2, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    o, v, X = DIMS
+    F = flops(o, v, X)
+    f = synth.fragment_inputs(o, v, X, seed=0)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    precs = ["bf16", "fp64"] if args.precision == "auto" else [args.precision]
+    results = {}
+    for prec in precs:
+        try:
+            eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev)
+        except rimp2.Rimp2Error as e:
+            if e.code == -8:
+                continue
+            raise
+        eng.set_inputs([f])
+        steps = args.steps if prec == precs[0] or args.precision != "auto" else args.fp64_steps
+        warm = args.warmup if prec == precs[0] or args.precision != "auto" else 1
+        for _ in range(warm):
+            eng.run()
+        barrier()
+        eng.check_status()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            e0.record(stream)
+            for _ in range(steps):
+                eng.run()
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        st = eng.plan.stats()
+        results[prec] = {"ms": ms, "steps": steps, "warmup": warm, "engine": eng,
+                         "clocks": clk.summary(), "launches": st.launches_per_call,
+                         "energy": float(eng.energy[0].item())}
+        if prec != precs[-1]:
+            pass
+    if not results:
+        raise RuntimeError("no precision path available")
+    head = precs[0] if precs[0] in results else list(results)[0]
+    R = results[head]
+    eng = R["engine"]
+
+    # end to end through the public API: pinned host inputs copied every step, energy read back
+    pinned_B = torch.from_numpy(f.B.reshape(-1)).pin_memory()
+    pinned_eps = torch.from_numpy(np.concatenate([f.eo, f.ev])).pin_memory()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        eng.B.copy_(pinned_B, non_blocking=True)
+        eng.eps.copy_(pinned_eps, non_blocking=True)
+        eng.run()
+        float(eng.energy[0].item())
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        eng.B.copy_(pinned_B, non_blocking=True)
+        eng.eps.copy_(pinned_eps, non_blocking=True)
+        eng.run()
+        float(eng.energy[0].item())   # device -> host read of the step's result
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    peaks, peak_src = load_peaks()
+    value = ws * F / (R["ms"] * 1e-3) / 1e12
+    if head == "fp64":
+        peak = 1.25  # nominal FP64 TFLOP/s of GB300 (CUDA-core DFMA), no measured figure
+        roof = {"bound": "alu", "achieved": F / (R["ms"] * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": F / (R["ms"] * 1e-3) / 1e12 / peak,
+                "traffic": None, "kernel": "k_gemm_f64 (whole step)",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+    else:
+        roof = R["engine"].plan and getattr(eng, "roofline", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": R["steps"], "warmup": R["warmup"], "ms_per_step": R["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "bf16",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, precision=head,
+                       l2="inputs larger than L2 (B 600 MB, workspace >> 129 MB); no flush",
+                       fragments_per_s=ws * 1000.0 / R["ms"], energy_Eh=R["energy"]),
+        "roofline": roof,
+        "e2e": {"value": ws * F / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": int(pinned_B.numel() * 8 + pinned_eps.numel() * 8),
+                "d2h_bytes_per_step": 8},
+        "gpu_launches": int(R["launches"] * R["steps"]),
+        "clocks": R["clocks"],
+        "paths": {p: {"ms_per_step": r["ms"], "tflops": F / (r["ms"] * 1e-3) / 1e12,
+                      "fragments_per_s": 1000.0 / r["ms"], "energy_Eh": r["energy"]}
+                  for p, r in results.items()},
+        "peaks": {"source": peak_src},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: val for k, val in cpu_baseline(f.B, f.eo, f.ev).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

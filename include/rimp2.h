@@ -1,0 +1,160 @@
+/*
+ * rimp2.h - C ABI of the GB300 (sm_103a) RI-MP2 energy and gradient-intermediate
+ * library (librimp2.so).
+ *
+ * What it computes, per fragment f of a batch (closed shell, no frozen core; Sec.
+ * "Notation" of arXiv 2410.21888 and its Appendix):
+ *
+ *   V_ij(a,b)  = sum_Q B^Q_ia B^Q_jb            RI integrals (ia|jb), Eq. MP2_ints
+ *   T_ij(a,b)  = V_ij(a,b) / (e_i + e_j - e_a - e_b)
+ *                                               amplitudes X^ab_ij (Appendix; the printed
+ *                                               denominator is garbled, this is the standard
+ *                                               sign)
+ *   Tt_ij(a,b) = 2 T_ij(a,b) - T_ij(b,a)        the 2X - X^T combination of Gamma
+ *   e_pair[i][j] = sum_ab Tt_ij(a,b) V_ij(a,b), E = sum_ij e_pair[i][j]
+ *                                               closed-shell MP2 energy
+ *   Gamma^Q_ia = sum_jb Tt_ij(a,b) B^Q_jb       Appendix Gamma in the MO-B basis (the
+ *                                               J^-1/2 back-transform is not applied)
+ *   P_ij = -sum_kab Tt_ik(a,b) T_jk(a,b)        Appendix D^MP2_ij (unrelaxed)
+ *   P_ab =  sum_ijc Tt_ij(a,c) T_ij(b,c)        Appendix D^MP2_ab (unrelaxed)
+ *
+ * Denominators, pair and cross-pair energy sums are FP64 in every precision mode.  In
+ * RIMP2_FP64 every contraction is FP64.  In the split modes the four contractions (V,
+ * Gamma, P_ab, P_ij) run on the tensor cores as sums of exact products of BF16 (or FP8)
+ * integer slices accumulated in FP32 and recombined at higher precision.
+ *
+ * Layouts (all row-major, element offsets into caller-owned device pools):
+ *   B[nocc][nvir][naux] FP64, naux fastest;  Gamma: same shape and layout as B;
+ *   eps: eps_occ[nocc] at eo_off, eps_vir[nvir] at ev_off (FP64);
+ *   P_ij[nocc][nocc], P_ab[nvir][nvir], e_pair[nocc][nocc] (FP64);
+ *   energy[nfrag] (FP64), one per fragment in batch order.
+ *
+ * Ownership: the caller owns every device buffer (inputs, outputs, workspace) and the
+ * stream.  A plan owns host metadata, a small device block (task queue counters,
+ * problem descriptors, status word) and the CUDA graph it captures.  Outputs are
+ * overwritten, never accumulated.
+ *
+ * Errors: every entry point returns RIMP2_OK (0) or a negative RIMP2_ERR_* code and
+ * never aborts, throws or traps.  Conditions that only the device can see (a
+ * denominator >= 0, non-finite inputs, an expired bounded wait) are recorded in the
+ * plan's status word; rimp2_get_status() reads it after synchronising the plan.
+ *
+ * Threading: a plan is used by one host thread and one stream at a time.
+ */
+#ifndef RIMP2_H
+#define RIMP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIMP2_OK 0
+#define RIMP2_ERR_BAD_ARG (-1)      /* null pointer, negative size, bad enum */
+#define RIMP2_ERR_SHAPE (-2)        /* batch shapes differ from the plan's */
+#define RIMP2_ERR_DENOM (-3)        /* some e_a <= e_i: a denominator is not negative */
+#define RIMP2_ERR_NONFINITE (-4)    /* NaN or Inf in B or the orbital energies */
+#define RIMP2_ERR_WORKSPACE (-5)    /* workspace pointer null/misaligned or too small */
+#define RIMP2_ERR_CUDA (-6)         /* a CUDA runtime call failed */
+#define RIMP2_ERR_TIMEOUT (-7)      /* a bounded device-side wait expired */
+#define RIMP2_ERR_UNSUPPORTED (-8)  /* option or size outside what this build supports */
+#define RIMP2_ERR_NOMEM (-9)        /* host or plan-internal device allocation failed */
+
+typedef enum {
+  RIMP2_FP64 = 0,        /* FP64 contractions (CUDA-core DFMA) */
+  RIMP2_BF16_SPLIT = 1,  /* BF16 integer-slice products on tcgen05, FP32 accumulate */
+  RIMP2_FP8_SPLIT = 2    /* reserved: FP8 (e4m3) slices */
+} rimp2_precision;
+
+/* One fragment: sizes and element offsets into the batch pools.  An offset of -1
+ * means "not requested" for gamma_off, pij_off, pab_off and epair_off. */
+typedef struct rimp2_frag {
+  int32_t nocc, nvir, naux, flags; /* flags: reserved, pass 0 */
+  int64_t b_off;                   /* into batch.B */
+  int64_t eo_off, ev_off;          /* into batch.eps */
+  int64_t gamma_off;               /* into batch.gamma, or -1 */
+  int64_t pij_off;                 /* into batch.pij, or -1 */
+  int64_t pab_off;                 /* into batch.pab, or -1 */
+  int64_t epair_off;               /* into batch.epair, or -1 */
+} rimp2_frag;
+
+/* Device pointers of one call.  frags is a host array of nfrag entries that must
+ * describe the same shapes, in the same order, as the plan's. */
+typedef struct rimp2_batch {
+  int32_t nfrag, reserved;
+  const rimp2_frag* frags;
+  const double* B;
+  const double* eps;
+  double* gamma;
+  double* pij;
+  double* pab;
+  double* epair;
+  double* energy; /* [nfrag], required */
+} rimp2_batch;
+
+typedef struct rimp2_options {
+  int32_t slices_v;    /* split modes: slices of B for V (2..8, default 5)        */
+  int32_t slices_t;    /* split modes: slices for Gamma/P operands (2..8, default 5) */
+  int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
+  int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
+  int32_t autotune;    /* 1: time tile variants in situ on first calls (default 0) */
+  int32_t reserved;
+  size_t max_workspace_bytes; /* 0: one wave for the whole batch; else waves sized so
+                                 the workspace stays below this many bytes */
+} rimp2_options;
+
+typedef struct rimp2_stats {
+  double flops_per_call;   /* algorithmic 2mnk count, V over pairs i<=j */
+  double last_ms;          /* device time of the last call (0 until measured) */
+  int64_t calls;
+  int64_t tiles_per_call;  /* work-queue entries popped per call */
+  int32_t launches_per_call; /* kernels launched per call */
+  int32_t waves;
+  int32_t graph_captures;
+  int32_t status;          /* last status word seen by rimp2_get_status */
+} rimp2_stats;
+
+typedef struct rimp2_plan rimp2_plan;
+
+/* Fills *opt with the defaults listed above. */
+void rimp2_default_options(rimp2_options* opt);
+
+/* Creates a plan for nfrag fragments with the given shapes (offsets are ignored here)
+ * and precision.  opt may be NULL (defaults).  Allocates the plan's small device block
+ * on the current device.  Returns RIMP2_ERR_BAD_ARG for null/negative inputs,
+ * RIMP2_ERR_UNSUPPORTED for an unknown precision or slice count. */
+int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
+                      const rimp2_options* opt, rimp2_plan** out);
+
+/* Bytes of device workspace rimp2_energy_grad needs (256-byte aligned pointer). */
+int rimp2_workspace_size(const rimp2_plan* plan, size_t* bytes);
+
+/* Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream): computes E
+ * for every fragment and Gamma / P_ij / P_ab / e_pair where requested.  workspace must
+ * hold rimp2_workspace_size() bytes; its contents are scratch.  Host-side validation
+ * errors return before anything is launched. */
+int rimp2_energy_grad(rimp2_plan* plan, const rimp2_batch* batch, void* workspace,
+                      size_t ws_bytes, void* stream);
+
+/* Synchronises the plan's last call and returns its device status: RIMP2_OK,
+ * RIMP2_ERR_DENOM, RIMP2_ERR_NONFINITE or RIMP2_ERR_TIMEOUT (the first one raised),
+ * or RIMP2_ERR_CUDA if synchronising failed.  Clears the status word. */
+int rimp2_get_status(rimp2_plan* plan);
+
+int rimp2_get_stats(const rimp2_plan* plan, rimp2_stats* out);
+
+void rimp2_plan_destroy(rimp2_plan* plan);
+
+/* Static description of a status code. */
+const char* rimp2_status_string(int status);
+
+/* Library build identification: "rimp2 <version> sm_103a". */
+const char* rimp2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIMP2_H */

@@ -1,0 +1,303 @@
+"""Python binding of librimp2 (ctypes).  Argument marshalling only: every step of the
+RI-MP2 hot path runs in the library's CUDA kernels; PyTorch provides device memory and
+streams.  There is no CPU fallback: without the built library on a CUDA machine the
+calls raise.
+
+Names follow include/rimp2.h: ``Plan`` wraps rimp2_plan_create / rimp2_energy_grad,
+``Engine`` owns device pools for a fixed batch of fragments, and ``energy_grad`` is the
+one-call convenience for a single fragment (host or device inputs).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librimp2.so")
+
+RIMP2_FP64 = 0
+RIMP2_BF16_SPLIT = 1
+PRECISIONS = {"fp64": RIMP2_FP64, "bf16": RIMP2_BF16_SPLIT, "bf16_split": RIMP2_BF16_SPLIT}
+
+ERRORS = {
+    -1: "BAD_ARG", -2: "SHAPE", -3: "DENOM", -4: "NONFINITE", -5: "WORKSPACE", -6: "CUDA",
+    -7: "TIMEOUT", -8: "UNSUPPORTED", -9: "NOMEM",
+}
+
+EXPORTED = ("rimp2_default_options", "rimp2_plan_create", "rimp2_workspace_size",
+            "rimp2_energy_grad", "rimp2_get_status", "rimp2_get_stats", "rimp2_plan_destroy",
+            "rimp2_status_string", "rimp2_version")
+
+
+class Rimp2Error(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: rimp2 status {code} ({ERRORS.get(code, '?')}: "
+                         f"{status_string(code) if _lib is not None else ''})")
+
+
+class Frag(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int32), ("nvir", ctypes.c_int32), ("naux", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("b_off", ctypes.c_int64), ("eo_off", ctypes.c_int64),
+                ("ev_off", ctypes.c_int64), ("gamma_off", ctypes.c_int64),
+                ("pij_off", ctypes.c_int64), ("pab_off", ctypes.c_int64),
+                ("epair_off", ctypes.c_int64)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("nfrag", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("frags", ctypes.POINTER(Frag)), ("B", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+                ("gamma", ctypes.c_void_p), ("pij", ctypes.c_void_p), ("pab", ctypes.c_void_p),
+                ("epair", ctypes.c_void_p), ("energy", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("slices_v", ctypes.c_int32), ("slices_t", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_workspace_bytes", ctypes.c_size_t)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("flops_per_call", ctypes.c_double), ("last_ms", ctypes.c_double),
+                ("calls", ctypes.c_int64), ("tiles_per_call", ctypes.c_int64),
+                ("launches_per_call", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("graph_captures", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librimp2.so (built in-tree by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librimp2.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.rimp2_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.rimp2_default_options.restype = None
+    lib.rimp2_plan_create.argtypes = [ctypes.POINTER(Frag), i32, i32, ctypes.POINTER(Options),
+                                      ctypes.POINTER(vp)]
+    lib.rimp2_plan_create.restype = ctypes.c_int
+    lib.rimp2_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.rimp2_workspace_size.restype = ctypes.c_int
+    lib.rimp2_energy_grad.argtypes = [vp, ctypes.POINTER(Batch), vp, ctypes.c_size_t, vp]
+    lib.rimp2_energy_grad.restype = ctypes.c_int
+    lib.rimp2_get_status.argtypes = [vp]
+    lib.rimp2_get_status.restype = ctypes.c_int
+    lib.rimp2_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.rimp2_get_stats.restype = ctypes.c_int
+    lib.rimp2_plan_destroy.argtypes = [vp]
+    lib.rimp2_plan_destroy.restype = None
+    lib.rimp2_status_string.argtypes = [ctypes.c_int]
+    lib.rimp2_status_string.restype = ctypes.c_char_p
+    lib.rimp2_version.argtypes = []
+    lib.rimp2_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().rimp2_status_string(int(code)).decode()
+
+
+def version() -> str:
+    return load().rimp2_version().decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise Rimp2Error(code, what)
+
+
+def default_options() -> Options:
+    o = Options()
+    load().rimp2_default_options(ctypes.byref(o))
+    return o
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("rimp2 needs a CUDA device (sm_103a); no CPU fallback exists")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """rimp2_plan for a fixed list of fragment shapes (nocc, nvir, naux)."""
+
+    def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 5,
+                 slices_t: int = 5, use_graph: bool = True, check_inputs: bool = True,
+                 max_workspace_bytes: int = 0):
+        _require_cuda()
+        lib = load()
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.precision = precision
+        frags = (Frag * max(1, len(self.dims)))()
+        for k, (o, v, X) in enumerate(self.dims):
+            frags[k].nocc, frags[k].nvir, frags[k].naux = o, v, X
+        opt = default_options()
+        opt.slices_v, opt.slices_t = int(slices_v), int(slices_t)
+        opt.use_graph, opt.check_inputs = int(use_graph), int(check_inputs)
+        opt.max_workspace_bytes = int(max_workspace_bytes)
+        h = ctypes.c_void_p()
+        _check(lib.rimp2_plan_create(frags, len(self.dims), PRECISIONS[precision],
+                                     ctypes.byref(opt), ctypes.byref(h)), "rimp2_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().rimp2_workspace_size(self._h, ctypes.byref(n)), "rimp2_workspace_size")
+        return int(n.value)
+
+    def energy_grad(self, batch: Batch, workspace: torch.Tensor, stream=None):
+        ws_ptr = workspace.data_ptr() if workspace is not None and workspace.numel() else None
+        ws_bytes = workspace.numel() * workspace.element_size() if ws_ptr else 0
+        _check(load().rimp2_energy_grad(self._h, ctypes.byref(batch), ws_ptr, ws_bytes,
+                                        _stream_handle(stream)), "rimp2_energy_grad")
+
+    def status(self) -> int:
+        return int(load().rimp2_get_status(self._h))
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(load().rimp2_get_stats(self._h, ctypes.byref(s)), "rimp2_get_stats")
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().rimp2_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Engine:
+    """Device pools + plan for a fixed batch of fragments.
+
+    ``set_inputs`` copies B / orbital energies (numpy or torch, host or device) into the
+    device pools; ``run`` launches the hot path; results stay in the device tensors
+    ``energy``, ``gamma``, ``pij``, ``pab``, ``epair`` (pools, see ``views``).
+    """
+
+    def __init__(self, dims: Sequence[tuple], precision: str = "fp64", want_gamma=True,
+                 want_p=True, want_epair=True, device="cuda", **plan_opts):
+        _require_cuda()
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.device = torch.device(device)
+        self.plan = Plan(self.dims, precision=precision, **plan_opts)
+        nb = sum(o * v * X for o, v, X in self.dims)
+        ne = sum(o + v for o, v, X in self.dims)
+        npij = sum(o * o for o, v, X in self.dims)
+        npab = sum(v * v for o, v, X in self.dims)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.B = torch.zeros(max(nb, 1), **f64)
+        self.eps = torch.zeros(max(ne, 1), **f64)
+        self.gamma = torch.zeros(max(nb, 1), **f64) if want_gamma else None
+        self.pij = torch.zeros(max(npij, 1), **f64) if want_p else None
+        self.pab = torch.zeros(max(npab, 1), **f64) if want_p else None
+        self.epair = torch.zeros(max(npij, 1), **f64) if want_epair else None
+        self.energy = torch.zeros(max(len(self.dims), 1), **f64)
+        ws = self.plan.workspace_size()
+        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        self._frags = (Frag * max(1, len(self.dims)))()
+        self.offsets = []
+        b = e = pij = pab = 0
+        for k, (o, v, X) in enumerate(self.dims):
+            fr = self._frags[k]
+            fr.nocc, fr.nvir, fr.naux, fr.flags = o, v, X, 0
+            fr.b_off, fr.eo_off, fr.ev_off = b, e, e + o
+            fr.gamma_off = b if want_gamma else -1
+            fr.pij_off = pij if want_p else -1
+            fr.pab_off = pab if want_p else -1
+            fr.epair_off = pij if want_epair else -1
+            self.offsets.append((b, e, pij, pab))
+            b += o * v * X
+            e += o + v
+            pij += o * o
+            pab += v * v
+        self._batch = Batch()
+        self._batch.nfrag = len(self.dims)
+        self._batch.frags = self._frags
+        self._batch.B = self.B.data_ptr()
+        self._batch.eps = self.eps.data_ptr()
+        self._batch.gamma = self.gamma.data_ptr() if want_gamma else None
+        self._batch.pij = self.pij.data_ptr() if want_p else None
+        self._batch.pab = self.pab.data_ptr() if want_p else None
+        self._batch.epair = self.epair.data_ptr() if want_epair else None
+        self._batch.energy = self.energy.data_ptr()
+
+    def set_inputs(self, frags, non_blocking=False):
+        """frags: sequence of objects with .B [o][v][X], .eo, .ev (numpy or torch)."""
+        for k, fr in enumerate(frags):
+            o, v, X = self.dims[k]
+            b, e, _, _ = self.offsets[k]
+            self.B[b:b + o * v * X].copy_(torch.as_tensor(fr.B).reshape(-1), non_blocking=non_blocking)
+            self.eps[e:e + o].copy_(torch.as_tensor(fr.eo), non_blocking=non_blocking)
+            self.eps[e + o:e + o + v].copy_(torch.as_tensor(fr.ev), non_blocking=non_blocking)
+
+    def run(self, stream=None):
+        self.plan.energy_grad(self._batch, self.workspace, stream=stream)
+
+    def check_status(self):
+        st = self.plan.status()
+        if st != 0:
+            raise Rimp2Error(st, "device status")
+
+    def views(self, k: int) -> dict:
+        """Per-fragment views of the output pools (device tensors)."""
+        o, v, X = self.dims[k]
+        b, e, pij, pab = self.offsets[k]
+        out = {"energy": self.energy[k]}
+        if self.gamma is not None:
+            out["gamma"] = self.gamma[b:b + o * v * X].view(o, v, X)
+        if self.pij is not None:
+            out["pij"] = self.pij[pij:pij + o * o].view(o, o)
+            out["pab"] = self.pab[pab:pab + v * v].view(v, v)
+        if self.epair is not None:
+            out["epair"] = self.epair[pij:pij + o * o].view(o, o)
+        return out
+
+
+def energy_grad(B, eo, ev, precision: str = "fp64", want_gamma=True, want_p=True, sync=True,
+                **plan_opts) -> dict:
+    """One fragment through the library: B[o][v][X], eps_occ[o], eps_vir[v] as numpy
+    arrays or torch tensors (host or device).  Returns device tensors."""
+    B_t = torch.as_tensor(B)
+    o, v, X = (int(x) for x in B_t.shape)
+    eng = Engine([(o, v, X)], precision=precision, want_gamma=want_gamma, want_p=want_p,
+                 **plan_opts)
+
+    class _F:
+        pass
+
+    f = _F()
+    f.B, f.eo, f.ev = B_t, torch.as_tensor(eo), torch.as_tensor(ev)
+    eng.set_inputs([f])
+    eng.run()
+    out = eng.views(0)
+    if sync:
+        torch.cuda.synchronize()
+        eng.check_status()
+    out["engine"] = eng
+    return out

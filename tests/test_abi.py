@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares (CPU only:
+no compute call is made without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2410_21888_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(rimp2_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = libbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for n in ("rimp2_plan_create", "rimp2_energy_grad", "rimp2_workspace_size",
+              "rimp2_plan_destroy", "rimp2_get_status", "rimp2_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(lib):
+    lib.rimp2_status_string.restype = ctypes.c_char_p
+    lib.rimp2_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.rimp2_version()
+    for code in range(0, -10, -1):
+        assert lib.rimp2_status_string(code)
+
+
+def test_plan_create_rejects_bad_args_without_gpu(lib):
+    """Host-side validation returns before touching the device."""
+    from paper_2410_21888_gb300 import rimp2
+    lib.rimp2_plan_create.argtypes = [ctypes.POINTER(rimp2.Frag), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(rimp2.Options), ctypes.POINTER(ctypes.c_void_p)]
+    h = ctypes.c_void_p()
+    assert lib.rimp2_plan_create(None, 1, 0, None, ctypes.byref(h)) == -1   # frags NULL
+    fr = (rimp2.Frag * 1)()
+    fr[0].nocc, fr[0].nvir, fr[0].naux = -1, 4, 4
+    assert lib.rimp2_plan_create(fr, 1, 0, None, ctypes.byref(h)) == -1     # negative size
+    fr[0].nocc = 2
+    assert lib.rimp2_plan_create(fr, 1, 7, None, ctypes.byref(h)) == -8     # bad precision
+    assert lib.rimp2_plan_create(fr, 1, 0, None, None) == -1                # out NULL
+
+
+def test_binding_fails_loudly_without_gpu():
+    import torch
+
+    from paper_2410_21888_gb300 import rimp2
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(RuntimeError):
+        rimp2.Plan([(2, 3, 4)])
