@@ -153,6 +153,37 @@ const char* rimp2_status_string(int status);
 /* Library build identification: "rimp2 <version> sm_103a". */
 const char* rimp2_version(void);
 
+/* ---- no-allocation entry point (the paper has no counterpart; library plumbing) ----
+ *
+ * For callers that must not allocate device memory: code running where cudaMalloc is
+ * forbidden or unsafe (inside a stream-ordered host callback, under an allocator that
+ * owns every byte of the device, in an embedding that audits allocations).  It computes
+ * the FP64 energy chain of ONE fragment - V, T = V / D, Tt, pair energies and
+ * E - with the same kernels as rimp2_energy_grad, but its scratch is a file-scope
+ * device array of RIMP2_NOALLOC_SCRATCH_BYTES that every GPU which loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments: B[nocc][nvir][naux] and eps[nocc + nvir] (occupied then virtual) are
+ * device FP64 inputs; energy (1 double) and epair ([nocc][nocc], or NULL) are device
+ * outputs, overwritten.  Asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).
+ *
+ * Limit: 4096 + 2 * align256(8 (nocc nvir)^2) + align256(8 nocc^2) bytes must fit in
+ * RIMP2_NOALLOC_SCRATCH_BYTES (about nocc * nvir <= 1440); larger fragments return
+ * RIMP2_ERR_WORKSPACE before anything is launched.  Negative sizes or NULL required
+ * pointers return RIMP2_ERR_BAD_ARG.
+ *
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current) and so should come before any stream capture.  All calls
+ * on a device share the one array and it keeps the last call's contents; each call
+ * clears what must start at zero.  Calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race on the array: serialise them. */
+#define RIMP2_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+int rimp2_energy_fp64_noalloc(int32_t nocc, int32_t nvir, int32_t naux, const double* B,
+                              const double* eps, double* energy, double* epair, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
