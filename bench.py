@@ -29,6 +29,10 @@ METRIC = "RI-MP2 energy+grad TFLOP/s and fragments/s on 1 GB300, vs plain FP64 a
 WORKLOAD = {"workload": "single fragment RI-MP2 energy+Gamma+P_ab+P_ij, nocc=100 nvir=500 "
                         "naux=1500, seed 0", "nocc": 100, "nvir": 500, "naux": 1500}
 DIMS = (100, 500, 1500)
+FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)
+# dram read+write bytes per launch of the dominant kernel from an ncu capture (None until
+# measured for the current kernel); keyed by stage index
+TRAFFIC_PER_LAUNCH = {}
 
 
 def flops(o, v, X):
@@ -197,25 +201,30 @@ def main():
     results = {}
     for prec in precs:
         try:
-            eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev)
+            eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True)
         except rimp2.Rimp2Error as e:
             if e.code == -8:
                 continue
             raise
         eng.set_inputs([f])
-        steps = args.steps if prec == precs[0] or args.precision != "auto" else args.fp64_steps
-        warm = args.warmup if prec == precs[0] or args.precision != "auto" else 1
+        head_run = prec == precs[0] or args.precision != "auto"
+        steps = args.steps if head_run else args.fp64_steps
+        warm = args.warmup if head_run else 1
         for _ in range(warm):
             eng.run()
         barrier()
         eng.check_status()
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage = [0.0, 0.0, 0.0, 0.0]
         with ClockSampler(local) as clk:
             barrier()
             e0.record(stream)
             for _ in range(steps):
                 eng.run()
+                st = eng.plan.stats()      # waits for the step; reads its stage timers
+                for k in range(4):
+                    stage[k] += st.stage_ms[k] / steps
             e1.record(stream)
             barrier()
         ms = e0.elapsed_time(e1) / steps
@@ -226,9 +235,9 @@ def main():
         st = eng.plan.stats()
         results[prec] = {"ms": ms, "steps": steps, "warmup": warm, "engine": eng,
                          "clocks": clk.summary(), "launches": st.launches_per_call,
-                         "energy": float(eng.energy[0].item())}
-        if prec != precs[-1]:
-            pass
+                         "energy": float(eng.energy[0].item()), "stage_ms": stage}
+        if not head_run:
+            del eng
     if not results:
         raise RuntimeError("no precision path available")
     head = precs[0] if precs[0] in results else list(results)[0]
@@ -259,34 +268,57 @@ def main():
 
     peaks, peak_src = load_peaks()
     value = ws * F / (R["ms"] * 1e-3) / 1e12
+    sm = R["stage_ms"]
+    F_v = float(o * (o + 1) * v * v * X)
+    F_c = F - F_v
     if head == "fp64":
-        peak = 1.25  # nominal FP64 TFLOP/s of GB300 (CUDA-core DFMA), no measured figure
-        roof = {"bound": "alu", "achieved": F / (R["ms"] * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": F / (R["ms"] * 1e-3) / 1e12 / peak,
-                "traffic": None, "kernel": "k_gemm_f64 (whole step)",
-                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
+        peak = FP64_PEAK_TFLOPS
+        k = 3 if sm[3] >= sm[1] else 1
+        Fk = F_c if k == 3 else F_v
+        ach = Fk / (sm[k] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "kernel": "k_gemm_f64 (" + ("Gamma/P_ab/P_ij" if k == 3 else "V") + ")",
+                "peak_source": "measured DFMA peak (probes/dfma_peak.cu)"}
     else:
-        roof = R["engine"].plan and getattr(eng, "roofline", None)
+        sv, stt = 5, 6
+        prod_v, prod_t = sv * (sv + 1) // 2, stt * (stt + 1) // 2
+        k = 3 if sm[3] >= sm[1] else 1
+        Fk = F_c * prod_t if k == 3 else F_v * prod_v
+        ach = Fk / (sm[k] * 1e-3) / 1e12
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get(k),
+                "kernel": "k_split_gemm (" + ("Gamma/P_ab/P_ij, 21 slice products"
+                                              if k == 3 else "V, 15 slice products") + ")",
+                "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)",
+                "fp64_equivalent_tflops": (F_c if k == 3 else F_v) / (sm[k] * 1e-3) / 1e12}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": R["steps"], "warmup": R["warmup"], "ms_per_step": R["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "bf16",
         "data": "synthetic",
-        "config": dict(WORKLOAD, precision=head,
+        "config": dict(WORKLOAD, precision=head if head == "fp64" else "bf16 split, 5 slices for V, "
+                                                                        "6 for Gamma/P",
                        l2="inputs larger than L2 (B 600 MB, workspace >> 129 MB); no flush",
                        fragments_per_s=ws * 1000.0 / R["ms"], energy_Eh=R["energy"]),
         "roofline": roof,
+        "stage_ms": {"slice_check": sm[0], "V_gemm": sm[1], "amplitudes_energy": sm[2],
+                     "gamma_p_gemm": sm[3]},
         "e2e": {"value": ws * F / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": int(pinned_B.numel() * 8 + pinned_eps.numel() * 8),
                 "d2h_bytes_per_step": 8},
         "gpu_launches": int(R["launches"] * R["steps"]),
         "clocks": R["clocks"],
         "paths": {p: {"ms_per_step": r["ms"], "tflops": F / (r["ms"] * 1e-3) / 1e12,
-                      "fragments_per_s": 1000.0 / r["ms"], "energy_Eh": r["energy"]}
+                      "fragments_per_s": 1000.0 / r["ms"], "energy_Eh": r["energy"],
+                      "stage_ms": r["stage_ms"]}
                   for p, r in results.items()},
         "peaks": {"source": peak_src},
     }
+    if "fp64" in results and head != "fp64":
+        line["config"]["energy_diff_vs_fp64_path_Eh"] = R["energy"] - results["fp64"]["energy"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: val for k, val in cpu_baseline(f.B, f.eo, f.ev).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

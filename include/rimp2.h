@@ -96,11 +96,12 @@ typedef struct rimp2_batch {
 
 typedef struct rimp2_options {
   int32_t slices_v;    /* split modes: slices of B for V (2..8, default 5)        */
-  int32_t slices_t;    /* split modes: slices for Gamma/P operands (2..8, default 5) */
+  int32_t slices_t;    /* split modes: slices for Gamma/P operands (2..8, default 6) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
   int32_t autotune;    /* 1: time tile variants in situ on first calls (default 0) */
-  int32_t reserved;
+  int32_t profile_stages; /* 1: record CUDA events between the stages of each call so that
+                             rimp2_get_stats reports stage_ms (default 0) */
   size_t max_workspace_bytes; /* 0: one wave for the whole batch; else waves sized so
                                  the workspace stays below this many bytes */
 } rimp2_options;
@@ -114,6 +115,10 @@ typedef struct rimp2_stats {
   int32_t waves;
   int32_t graph_captures;
   int32_t status;          /* last status word seen by rimp2_get_status */
+  double stage_ms[4];      /* with profile_stages: device ms of the last call, summed over
+                              waves: [0] input checks and operand slicing, [1] V GEMM with the
+                              T = V/D epilogue, [2] amplitudes, pair/total energies, zeroing,
+                              [3] Gamma / P_ab / P_ij contractions */
 } rimp2_stats;
 
 typedef struct rimp2_plan rimp2_plan;
@@ -143,7 +148,8 @@ int rimp2_energy_grad(rimp2_plan* plan, const rimp2_batch* batch, void* workspac
  * or RIMP2_ERR_CUDA if synchronising failed.  Clears the status word. */
 int rimp2_get_status(rimp2_plan* plan);
 
-int rimp2_get_stats(const rimp2_plan* plan, rimp2_stats* out);
+/* Copies the plan's counters; with profile_stages it first waits for the last call. */
+int rimp2_get_stats(rimp2_plan* plan, rimp2_stats* out);
 
 void rimp2_plan_destroy(rimp2_plan* plan);
 

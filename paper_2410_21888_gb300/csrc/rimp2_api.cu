@@ -70,6 +70,7 @@ struct rimp2_plan {
   bool timing_pending = false;
   rimp2_stats stats{};
   SplitPlan split;
+  std::vector<cudaEvent_t> stage_ev;   // 5 per wave when profile_stages
 };
 
 extern "C" {
@@ -96,7 +97,7 @@ void rimp2_default_options(rimp2_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
   opt->slices_v = 5;
-  opt->slices_t = 5;
+  opt->slices_t = 6;
   opt->use_graph = 1;
   opt->check_inputs = 1;
   opt->autotune = 0;
@@ -114,7 +115,7 @@ size_t frag_ws_elems_fp64(const rimp2_frag& f) {
 
 size_t frag_ws_elems(const rimp2_plan* p, const rimp2_frag& f) {
   if (p->precision == RIMP2_FP64) return frag_ws_elems_fp64(f);
-  return split_frag_ws_elems(p->split, f);
+  return (split_frag_ws_bytes(p->split, f) + 7) / 8;
 }
 
 int check_frag_shapes(const rimp2_frag* frags, int nfrag) {
@@ -230,14 +231,14 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
   finish_probs(w.probs_c, w.tiles_c);
 }
 
-int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags) {
+int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags, const double* B, void* ws) {
   p->waves.clear();
   for (auto& m : p->wave_members) {
     WaveDesc w;
     w.frags = m;
     if (p->precision == RIMP2_FP64) build_fp64_wave(p, frags, w);
     else {
-      int rc = split_build_wave(p->split, frags, m, w.fdev, w.split, w.total_pairs, w.max_b);
+      int rc = split_build_wave(p->split, frags, m, B, ws, w.fdev, w.split, w.total_pairs, w.max_b);
       if (rc != RIMP2_OK) return rc;
     }
     p->waves.push_back(std::move(w));
@@ -292,30 +293,36 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
     const int nf = (int)w.fdev.size();
     unsigned* ctr = p->d_counters + wi * 8;
     cudaError_t e = cudaSuccess;
+    cudaEvent_t* ev = p->opt.profile_stages ? &p->stage_ev[wi * 5] : nullptr;
+    if (ev && cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal) != cudaSuccess) return RIMP2_ERR_CUDA;
     if (p->opt.check_inputs) {
       e = launch_check_inputs(dfd, nf, (w.max_b + 255) / 256, bs, s);
       ++launches;
       if (e != cudaSuccess) return RIMP2_ERR_CUDA;
     }
     if (p->precision == RIMP2_FP64) {
+      if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
       e = launch_gemm_f64((const GemmProb*)(p->dblk + w.off_pv), (int)w.probs_v.size(), w.tiles_v,
                           bs, ctr + 0, p->gemm_grid, s);
       launches += w.tiles_v > 0;
+      if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
       if (e == cudaSuccess) { e = launch_amplitude_f64(dfd, nf, w.total_pairs, bs, s); launches += w.total_pairs > 0; }
       if (e == cudaSuccess) { e = launch_energy_reduce(dfd, nf, bs, s); ++launches; }
       if (e == cudaSuccess) { e = launch_zero_p(dfd, nf, bs, s); ++launches; }
+      if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
       if (e == cudaSuccess) {
         e = launch_gemm_f64((const GemmProb*)(p->dblk + w.off_pc), (int)w.probs_c.size(), w.tiles_c,
                             bs, ctr + 1, p->gemm_grid, s);
         launches += w.tiles_c > 0;
       }
       tiles += w.tiles_v + w.tiles_c;
+      if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
       if (e != cudaSuccess) return RIMP2_ERR_CUDA;
     } else {
       int nl = 0;
       long long nt = 0;
       int rc = split_enqueue_wave(p->split, w.split, p->dblk, dfd, nf, w.total_pairs, bs, ctr, s,
-                                  &nl, &nt);
+                                  &nl, &nt, ev);
       launches += nl;
       tiles += nt;
       if (rc != RIMP2_OK) return rc;
@@ -395,6 +402,11 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
     rimp2_plan_destroy(p);
     return RIMP2_ERR_CUDA;
   }
+  if (o.profile_stages) {
+    p->stage_ev.assign(p->wave_members.size() * 5, nullptr);
+    for (auto& e : p->stage_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); rimp2_plan_destroy(p); return RIMP2_ERR_CUDA; }
+  }
   // device block with a zero status word
   p->dblk_bytes = 4096;
   if (cudaMalloc(&p->dblk, p->dblk_bytes) != cudaSuccess) {
@@ -443,7 +455,7 @@ int rimp2_energy_grad(rimp2_plan* p, const rimp2_batch* b, void* workspace, size
   if (changed) {
     if (cudaEventSynchronize(p->done) != cudaSuccess) return RIMP2_ERR_CUDA;
     drop_graph(p);
-    int rc = upload_descriptors(p, b->frags);
+    int rc = upload_descriptors(p, b->frags, b->B, workspace);
     if (rc != RIMP2_OK) { p->have_desc = false; return rc; }
     p->key = k;
   }
@@ -509,8 +521,19 @@ int rimp2_get_status(rimp2_plan* p) {
   return rc;
 }
 
-int rimp2_get_stats(const rimp2_plan* p, rimp2_stats* out) {
+int rimp2_get_stats(rimp2_plan* p, rimp2_stats* out) {
   if (!p || !out) return RIMP2_ERR_BAD_ARG;
+  if (p->opt.profile_stages && p->stats.calls > 0) {
+    if (cudaEventSynchronize(p->done) != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
+    for (int k = 0; k < 4; ++k) p->stats.stage_ms[k] = 0.0;
+    for (size_t w = 0; w < p->wave_members.size(); ++w)
+      for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->stage_ev[w * 5 + k], p->stage_ev[w * 5 + k + 1]) == cudaSuccess)
+          p->stats.stage_ms[k] += ms;
+        cudaGetLastError();
+      }
+  }
   *out = p->stats;
   return RIMP2_OK;
 }
@@ -525,6 +548,8 @@ void rimp2_plan_destroy(rimp2_plan* p) {
   if (p->done) cudaEventDestroy(p->done);
   if (p->t0) cudaEventDestroy(p->t0);
   if (p->t1) cudaEventDestroy(p->t1);
+  for (auto e : p->stage_ev)
+    if (e) cudaEventDestroy(e);
   cudaGetLastError();
   delete p;
 }

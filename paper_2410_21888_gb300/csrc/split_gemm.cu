@@ -1,0 +1,566 @@
+// Split-precision tensor-core GEMM for sm_103a: TMA-fed, tcgen05.mma (kind::f16, BF16
+// in, FP32 TMEM accumulators), one persistent CTA per SM pulling tiles from a device
+// queue in LPT order.  Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues
+// the MMAs from one thread, warps 2..9 drain TMEM every 256-K chunk into double-float
+// registers and run the problem's epilogue.
+//
+// Every mbarrier wait is bounded (globaltimer, 2 s): on expiry the CTA records
+// ST_TIMEOUT in the status word, stops all roles, waits (bounded) for its own TMA
+// loads in flight, frees its TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include "split_gemm.cuh"
+
+namespace rimp2 {
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a healthy wait takes microseconds
+
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > limit_ns) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar, int c0,
+                                       int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar, int c0,
+                                       int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar, int c0,
+                                       int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(dst),
+      "l"(tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+               : "r"(taddr)
+               : "memory");
+  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+  v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5);
+  v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// UMMA shared-memory descriptor, K-major operand with 64-byte swizzle: rows of 64 bytes,
+// 8-row core groups 512 bytes apart (SBO), descriptor version 1, layout SWIZZLE_64B (4).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(512u >> 4) << 32) |
+         ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
+}
+
+// ------------------------------------------------------------------ double-float
+
+struct df { float h, l; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+
+// a / b with a correction step on the exact remainder (Dekker-style double-length
+// division): q1 = a_h / b_h, r = a - q1 b (q1 b_h formed exactly with an FMA), q2 = r / b_h.
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = a.h / b.h;
+  const float ph = q1 * b.h;
+  const float pl = fmaf(q1, b.h, -ph);
+  const float r = (((a.h - ph) - pl) + a.l) - q1 * b.l;
+  const float q2 = r / b.h;
+  return fast_two_sum(q1, q2);
+}
+
+// 2^e as float for e in [-252, 254] via two normal factors
+__device__ __forceinline__ void pow2_pair(int e, float& s1, float& s2) {
+  e = max(-252, min(254, e));
+  const int e1 = e / 2, e2 = e - e1;
+  s1 = __int_as_float((e1 + 127) << 23);
+  s2 = __int_as_float((e2 + 127) << 23);
+}
+
+// ------------------------------------------------------------------ tile decode
+
+struct TileInfo {
+  const SplitProb* P;
+  int tm, tn, k1b, k1e, nK;
+  bool skip;
+};
+
+__device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ probs, int nprobs,
+                                                long long t, int nt) {
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  TileInfo ti;
+  ti.P = probs + lo;
+  const long long lt = t - ti.P->tile_begin;
+  const int ks = (int)(lt % ti.P->ksplit);
+  const long long tt = lt / ti.P->ksplit;
+  ti.tm = (int)(tt / ti.P->tiles_n);
+  ti.tn = (int)(tt % ti.P->tiles_n);
+  ti.k1b = ks * ti.P->k1_chunk;
+  ti.k1e = min(ti.P->k1_count, ti.k1b + ti.P->k1_chunk);
+  ti.nK = max(0, ti.k1e - ti.k1b) * ti.P->k0_blocks;
+  // V is symmetric: tiles whose every row index exceeds every column index are covered
+  // by the mirrored writes of the transposed tile
+  ti.skip = (ti.P->kind == PK_V) && (ti.tm * SG_BM > ti.tn * nt + nt - 1);
+  if (ti.skip) ti.nK = 0;
+  return ti;
+}
+
+__device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int mode, int x, int row, int k1, int div5, int slice) {
+  if (mode == TM_3D) tma_3d(dst, tm, bar, x, row, slice);
+  else if (mode == TM_4D) tma_4d(dst, tm, bar, x, row, k1, slice);
+  else tma_5d(dst, tm, bar, x, k1 / div5, k1 % div5, row, slice);
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <int NT>
+__global__ void __launch_bounds__(SG_THREADS, 1)
+k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, Bases bs,
+             unsigned* __restrict__ counter, int slices, int stages) {
+  constexpr int NC = NT / 2;                 // columns per epilogue thread
+  constexpr uint32_t A_TILE = SG_BM * 64;    // bytes of one 128 x 32 bf16 tile
+  constexpr uint32_t B_TILE = NT * 64;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t stage_bytes = (uint32_t)slices * (A_TILE + B_TILE);
+  uint64_t* full = (uint64_t*)(smem + (size_t)stages * stage_bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* tmem_full = empty + stages;
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint64_t* tile_full = tmem_empty + 1;      // [2]
+  uint64_t* tile_empty = tile_full + 2;      // [2]
+  long long* tile_idx = (long long*)(tile_empty + 2);  // [2]
+  uint32_t* tmem_base_slot = (uint32_t*)(tile_idx + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_base_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(tmem_full, 1);
+    mbar_init(tmem_empty, SG_EPI_WARPS);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(tile_full + s, 1);
+      mbar_init(tile_empty + s, 1 + SG_EPI_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_base_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0;
+      int tslot = 0;
+      uint32_t tph = 0;
+      bool pending[8] = {false, false, false, false, false, false, false, false};
+      uint32_t pend_ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (;;) {
+        const long long t = (long long)atomicAdd(counter, 1u);
+        if (!mbar_wait(tile_empty + tslot, tph ^ 1u, abort_flag)) break;
+        tile_idx[tslot] = t;
+        mbar_arrive(tile_full + tslot);
+        tslot ^= 1;
+        if (tslot == 0) tph ^= 1u;
+        if (t >= total) break;
+        const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+        const SplitProb* P = ti.P;
+        const int rowA = ti.tm * SG_BM, rowB = ti.tn * NT;
+        bool ok = true;
+        for (int kk = 0; kk < ti.nK; ++kk) {
+          if (!mbar_wait(empty + st, ph ^ 1u, abort_flag)) { ok = false; break; }
+          pending[st] = false;
+          mbar_arrive_expect_tx(full + st, stage_bytes);
+          pending[st] = true;
+          pend_ph[st] = ph;
+          const int k1 = ti.k1b + kk / P->k0_blocks;
+          const int x = (kk % P->k0_blocks) * SG_BK;
+          const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
+          for (int p = 0; p < slices; ++p)
+            tma_operand(base + p * A_TILE, &P->tmA, full + st, P->a_mode, x, rowA, k1, P->div5, p);
+          for (int q = 0; q < slices; ++q)
+            tma_operand(base + slices * A_TILE + q * B_TILE, &P->tmB, full + st, P->b_mode, x, rowB,
+                        k1, P->div5, q);
+          if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag) {
+        // let our own copies in flight land before the CTA leaves (bounded)
+        for (int s = 0; s < stages && s < 8; ++s)
+          if (pending[s]) {
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(full + s, pend_ph[s]) && global_ns() - t0 < 100000000ull) { }
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                             ((uint32_t)(SG_BM >> 4) << 24);
+      uint32_t st = 0, ph = 0, te_count = 0;
+      int tslot = 0;
+      uint32_t tph = 0;
+      for (;;) {
+        if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
+        const long long t = tile_idx[tslot];
+        mbar_arrive(tile_empty + tslot);
+        tslot ^= 1;
+        if (tslot == 0) tph ^= 1u;
+        if (t >= total) break;
+        const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+        const int chunks = (ti.nK + SG_CHUNK_STAGES - 1) / SG_CHUNK_STAGES;
+        bool ok = true;
+        for (int c = 0; c < chunks && ok; ++c) {
+          if (!mbar_wait(tmem_empty, (te_count & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          ++te_count;
+          tc_fence_after();
+          const int kend = min(ti.nK, (c + 1) * SG_CHUNK_STAGES);
+          for (int kk = c * SG_CHUNK_STAGES; kk < kend; ++kk) {
+            if (!mbar_wait(full + st, ph, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
+#pragma unroll
+            for (int k16 = 0; k16 < 2; ++k16) {
+              for (int p = 0; p < slices; ++p) {
+                const uint64_t adesc = sw64_desc(base + p * A_TILE) + (uint64_t)(k16 * 2);
+                for (int q = 0; q + p < slices; ++q) {
+                  const uint64_t bdesc =
+                      sw64_desc(base + slices * A_TILE + q * B_TILE) + (uint64_t)(k16 * 2);
+                  const uint32_t acc = (kk == c * SG_CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
+                  umma_bf16(tmem_base + (uint32_t)((p + q) * NT), adesc, bdesc, idesc, acc);
+                }
+              }
+            }
+            umma_commit(empty + st);   // frees this smem stage once its MMAs completed
+            if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
+          }
+          if (ok) umma_commit(tmem_full);
+        }
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int ew = warp - 2;                   // 0..7
+    const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
+    const int c0 = (ew >> 2) * NC;             // first column of this thread
+    const int row = quad * 32 + lane;          // row within the tile
+    const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
+    uint32_t tf_count = 0;
+    int tslot = 0;
+    uint32_t tph = 0;
+    for (;;) {
+      if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
+      const long long t = tile_idx[tslot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tile_empty + tslot);
+      tslot ^= 1;
+      if (tslot == 0) tph ^= 1u;
+      if (t >= total) break;
+      const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+      if (ti.skip) continue;
+      const int chunks = (ti.nK + SG_CHUNK_STAGES - 1) / SG_CHUNK_STAGES;
+      float acc_h[NC], acc_l[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { acc_h[c] = 0.f; acc_l[c] = 0.f; }
+      bool ok = true;
+      for (int ch = 0; ch < chunks; ++ch) {
+        if (!mbar_wait(tmem_full, tf_count & 1u, abort_flag)) { ok = false; break; }
+        ++tf_count;
+        tc_fence_after();
+        for (int l = 0; l < slices; ++l) {
+          float v[NC];
+#pragma unroll
+          for (int g = 0; g < NC / 8; ++g)
+            tmem_ld8(lane_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
+          tmem_wait_ld();
+          const float sc = __int_as_float((127 - 8 * l) << 23);   // 2^(-8 l)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const df s = two_sum(acc_h[c], v[c] * sc);
+            acc_h[c] = s.h;
+            acc_l[c] += s.l;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tmem_empty);
+      }
+      if (!ok) break;
+      // ---------------- problem epilogue (registers only; TMEM already released)
+      const SplitProb* P = ti.P;
+      const int m = ti.tm * SG_BM + row;
+      unsigned emax = 0;
+      if (m < P->M) {
+        const int nbase = ti.tn * NT + c0;
+        const char* wsb = (const char*)bs.ws;
+        const int* EA = (const int*)(wsb + P->ea_off);
+        const int* EB = (const int*)(wsb + P->eb_off);
+        const int ea = (P->ea_rows ? EA[m] : EA[0]) + P->ea_add;
+        if (P->kind == PK_V) {
+          float* Th = (float*)(wsb + P->c_off);
+          float* Tl = (float*)(wsb + P->c2_off);
+          const float2* dv = (const float2*)(wsb + P->d_off);
+          const float2 dm = dv[m];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int n = nbase + c;
+            if (n >= P->N) continue;
+            float s1, s2;
+            pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 16, s1, s2);
+            const df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
+            const float2 dn = dv[n];
+            const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
+            const df T = df_div(V, D);
+            Th[(long long)m * P->ldc + n] = T.h;
+            Tl[(long long)m * P->ldc + n] = T.l;
+            Th[(long long)n * P->ldc + m] = T.h;
+            Tl[(long long)n * P->ldc + m] = T.l;
+            emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
+          }
+        } else {
+          double* C = (P->kind == PK_GAMMA || P->kind == PK_RAW) ? bs.gamma
+                      : P->kind == PK_PAB ? bs.pab : bs.pij;
+          C += P->c_off;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int n = nbase + c;
+            if (n >= P->N) continue;
+            const int e = ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 16;
+            const double val = ldexp((double)acc_h[c] + (double)acc_l[c], e);
+            if ((P->kind == PK_GAMMA || P->kind == PK_RAW) && P->ksplit == 1)
+              C[(long long)m * P->ldc + n] = P->alpha * val;
+            else
+              atomicAdd(C + (long long)m * P->ldc + n, P->alpha * val);
+          }
+        }
+      }
+      if (P->kind == PK_V) {   // uniform across the warp
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0 && emax) atomicMax((unsigned*)((char*)bs.ws + P->et_off), emax);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- teardown
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(bs.status, ST_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512u)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+SplitLaunch split_launch_config(int slices) {
+  SplitLaunch c{};
+  c.slices = slices;
+  c.n_tile_max = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
+  const size_t stage = (size_t)slices * (SG_BM * 64 + c.n_tile_max * 64);
+  const size_t budget = 227 * 1024 - 1024 - 256;
+  int st = (int)(budget / stage);
+  if (st > 4) st = 4;
+  if (st < 1) st = 1;
+  c.stages = st;
+  c.smem = 1024 + (size_t)st * stage + 256;
+  return c;
+}
+
+template <int NT>
+static cudaError_t launch_nt(const SplitProb* d_probs, int nprobs, long long total, Bases bs,
+                             unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
+  k_split_gemm<NT><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs, counter,
+                                                     cfg.slices, cfg.stages);
+  return cudaGetLastError();
+}
+
+// Opt in to the large dynamic shared memory once per device, outside any capture.
+cudaError_t split_gemm_prepare() {
+  const int bytes = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_split_gemm<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_split_gemm<80>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles, Bases bs,
+                              unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const long long g = total_tiles < grid ? total_tiles : grid;
+  switch (cfg.n_tile_max) {
+    case 96: return launch_nt<96>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    case 80: return launch_nt<80>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    default: return launch_nt<64>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+  }
+}
+
+int split_gemm_grid() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;  // one persistent CTA per SM (TMEM 512 columns and ~210 KB smem each)
+}
+
+int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
+                const uint64_t* strides_bytes, const uint32_t* box) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return RIMP2_ERR_CUDA;
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  cuuint64_t d[5], s[4];
+  cuuint32_t b[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    es[i] = 1;
+    if (i > 0) s[i - 1] = strides_bytes[i - 1];
+  }
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
+                        d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RIMP2_OK : RIMP2_ERR_UNSUPPORTED;
+}
+
+}  // namespace rimp2

@@ -1,0 +1,81 @@
+// Split-precision tensor-core GEMM (tcgen05, sm_103a): shared declarations.
+//
+// Operands are "slices": balanced base-256 integer digits d_p in [-128, 128] of FP64
+// values relative to a power-of-two scale, stored as BF16 (exact for such integers):
+//   x ~= sum_p d_p 2^(E - 8(p+1)),   |x| < 2^(E-1).
+// C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 16) sum_l 2^(-8 l) S_l with
+// S_l = sum_{p+q=l} sum_k dA_p dB_q, the truncated level sum kept for l < s.  Each S_l
+// accumulates in its own FP32 TMEM accumulator over K chunks of 256, where levels 0..3
+// are exact integers (|S_l| <= 4 * 256 * 2^14 = 2^24); each chunk is then folded into
+// a per-element double-float (hi, lo) accumulator in registers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rimp2_internal.cuh"
+
+namespace rimp2 {
+
+constexpr int SG_BM = 128;          // rows per tile (TMEM lanes)
+constexpr int SG_BN_MAX = 96;       // max columns per tile
+constexpr int SG_BK = 32;           // bf16 K elements per stage (64-byte rows, 64B swizzle)
+constexpr int SG_CHUNK_STAGES = 8;  // 256 K per exact accumulation chunk
+constexpr int SG_MAX_SLICES = 8;
+constexpr int SG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int SG_EPI_WARPS = 8;
+
+// TMA coordinate modes of one operand
+enum : int {
+  TM_3D = 0,    // {k0*32, row, slice}
+  TM_4D = 1,    // {k0*32, row, k1, slice}
+  TM_5D = 2,    // {k0*32, k1 / div, k1 % div, row, slice}
+};
+
+// Extra problem kind used only by the testing hook: store sum_l 2^-8l S_l * 2^(EA+EB-16)
+constexpr int PK_RAW = 7;
+
+struct SplitProb {  // 64-byte aligned through its CUtensorMap members
+  CUtensorMap tmA;        // A slices, box {32, 128, ...}
+  CUtensorMap tmB;        // B slices, box {32, n_tile, ...}
+  int kind, frag;
+  int M, N, n_tile;
+  int tiles_m, tiles_n, ksplit;
+  int k0_blocks;          // 32-wide blocks of the inner (contiguous) K dimension
+  int k1_count, k1_chunk; // outer K index range and its per-split chunk
+  int a_mode, b_mode, div5;
+  int ea_rows, eb_rows;   // 1: per-row int32 exponent array; 0: one int32 scalar
+  int ea_add, eb_add;     // added to the stored exponent
+  int pad0;
+  long long tile_begin, ntiles;
+  long long ea_off, eb_off;   // byte offsets into the workspace (int32 data)
+  long long c_off, c2_off;    // outputs: PK_V: byte offsets of T_hi / T_lo planes in ws;
+                              // others: element offsets into gamma / pab / pij
+  long long ldc;
+  double alpha;
+  long long d_off;            // PK_V: byte offset of float2 d_m = e_i - e_a per row
+  long long et_off;           // PK_V: byte offset of the unsigned max-exponent slot of |T|
+  int v;                      // PK_V: nvir of the fragment
+  int pad1;
+};
+
+struct SplitLaunch {
+  int slices;     // s (levels); same for every problem of one launch
+  int n_tile_max; // widest n_tile of the launch (smem layout)
+  int stages;     // pipeline depth
+  size_t smem;    // dynamic shared memory bytes
+};
+
+SplitLaunch split_launch_config(int slices);
+cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles,
+                              Bases bs, unsigned* counter, const SplitLaunch& cfg, int grid,
+                              cudaStream_t s);
+int split_gemm_grid();
+cudaError_t split_gemm_prepare();
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
+                const uint64_t* strides_bytes, const uint32_t* box);
+
+}  // namespace rimp2

@@ -1,29 +1,601 @@
-// Split-precision path (placeholder until the tensor-core kernels land).
+// Split-precision path of the RI-MP2 hot path (precision RIMP2_BF16_SPLIT).
+//
+// Per wave of fragments:
+//   1. k_split_reset   per-fragment exponent slots
+//   2. k_slice_b1      B -> balanced base-256 digits with one scale per row (i,a): the
+//                      operands of V (Eq. MP2_ints); also d_m = e_i - e_a per row
+//   3. k_slice_b2      B -> digits with one scale per fragment, transposed to [Q][(j,b)]:
+//                      the B operand of Gamma
+//   4. split GEMM      V on the tensor cores, epilogue T = V / D kept as a double-float
+//                      pair of planes (both triangles), max |T| exponent
+//   5. k_amp_split     Tt = 2T - T^T, pair energies e_ij (FP64 per pair), digits of Tt and
+//                      T with one scale per fragment
+//   6. energy reduce   FP64 compensated cross-pair sum (shared with the FP64 path)
+//   7. zero P, split GEMM for Gamma, P_ab and P_ij (Appendix Gamma, D^MP2_ab, D^MP2_ij)
+#include <climits>
 #include <cstring>
+#include <algorithm>
+
+#include <cuda_bf16.h>
 
 #include "split_path.cuh"
 
 namespace rimp2 {
 
+namespace {
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ device helpers
+
+struct dfl { float h, l; };
+
+__device__ __forceinline__ dfl d_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl d_fast(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl d_add(dfl a, dfl b) {
+  dfl s = d_two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return d_fast(s.h, s.l);
+}
+__device__ __forceinline__ dfl d_neg(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfl d_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return d_fast(p, e);
+}
+__device__ __forceinline__ dfl d_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ int find_sfd(const SplitFragDev* __restrict__ f, int n, long long t,
+                                        int which) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const long long k = which == 0 ? f[mid].row_begin : which == 1 ? f[mid].b2_tile_begin
+                                                                   : f[mid].pair_begin;
+    if (k <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void tri_rc(long long t, int& r, int& c) {
+  long long cc = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (cc * (cc + 1) / 2 > t) --cc;
+  while ((cc + 1) * (cc + 2) / 2 <= t) ++cc;
+  c = (int)cc;
+  r = (int)(t - cc * (cc + 1) / 2);
+}
+
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(float d) { return __float2bfloat16_rn(d); }
+
+// Digits of an FP64 value x relative to 2^E (|x| < 2^(E-1)): X = x 2^(8-E),
+// d_p = rint(X), X <- 256 (X - d_p); every step is exact in FP64.
+__device__ __forceinline__ void digits_f64(double x, int E, int s, __nv_bfloat16* out,
+                                           long long plane) {
+  double X = ldexp(x, 8 - E);
+  for (int p = 0; p < s; ++p) {
+    const double d = rint(X);
+    out[p * plane] = digit_bf16((float)d);
+    X = (X - d) * 256.0;
+  }
+}
+
+// Same for a double-float (h, l): d_p = rint(X_h); the remainder (X_h - d_p) is exact and
+// is re-joined with X_l by an error-free sum before the next scaling by 256.
+__device__ __forceinline__ void digits_df(dfl x, int E, int s, __nv_bfloat16* out,
+                                          long long plane) {
+  const int e = max(-252, min(254, 8 - E));
+  const int e1 = e / 2, e2 = e - e1;
+  const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
+  float xh = (x.h * s1) * s2, xl = (x.l * s1) * s2;
+  for (int p = 0; p < s; ++p) {
+    const float d = rintf(xh);
+    out[p * plane] = digit_bf16(d);
+    const dfl r = d_two_sum(xh - d, xl);
+    xh = r.h * 256.f;
+    xl = r.l * 256.f;
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases bs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int* sc = (int*)((char*)bs.ws + f[i].scal);
+  sc[0] = -1000;   // below any exponent a nonzero B element can have (atomicMax target)
+  sc[1] = 0;
+}
+
+// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, and the
+// fragment-wide maximum exponent used by the Gamma operand.
+__global__ void __launch_bounds__(256)
+k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, Bases bs) {
+  const long long gr = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gr >= rows) return;
+  const SplitFragDev& F = f[find_sfd(f, nf, gr, 0)];
+  const int r = (int)(gr - F.row_begin);
+  const double* x = bs.B + F.b_off + (long long)r * F.X;
+  double mx = 0.0;
+  for (int q = lane; q < F.X; q += 32) mx = fmax(mx, fabs(x[q]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
+  char* ws = (char*)bs.ws;
+  const long long plane = (long long)F.o * F.v * F.xpad;
+  __nv_bfloat16* out = (__nv_bfloat16*)(ws + F.bs1) + (long long)r * F.xpad;
+  for (int q = lane; q < F.X; q += 32) digits_f64(x[q], E, sv, out + q, plane);
+  if (lane == 0) {
+    ((int*)(ws + F.erow))[r] = E;
+    const int i = r / F.v, a = r - i * F.v;
+    const dfl d = d_from(bs.eps[F.eo_off + i] - bs.eps[F.ev_off + a]);
+    ((float2*)(ws + F.drow))[r] = make_float2(d.h, d.l);
+    if (mx > 0.0) atomicMax((int*)(ws + F.scal), E);
+  }
+}
+
+// Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale per
+// fragment.  32 x 32 tiles transposed through shared memory.
+__global__ void __launch_bounds__(256)
+k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
+  __shared__ double tile[32][33];
+  const long long gt = blockIdx.x;
+  const SplitFragDev& F = f[find_sfd(f, nf, gt, 1)];
+  const long long lt = gt - F.b2_tile_begin;
+  const int RL = F.o * F.vpad;
+  const int ntc = (RL + 31) / 32;
+  const int tq = (int)(lt / ntc), tc = (int)(lt % ntc);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double* B = bs.B + F.b_off;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = tc * 32 + r, Q = tq * 32 + tx;
+    double val = 0.0;
+    if (c < RL && Q < F.X) {
+      const int j = c / F.vpad, b = c - j * F.vpad;
+      if (b < F.v) val = B[((long long)j * F.v + b) * F.X + Q];
+    }
+    tile[r][tx] = val;
+  }
+  __syncthreads();
+  char* ws = (char*)bs.ws;
+  const int E = *(const int*)(ws + F.scal);
+  const long long plane = (long long)F.X * RL;
+  __nv_bfloat16* out = (__nv_bfloat16*)(ws + F.bs2);
+  for (int r = ty; r < 32; r += 8) {
+    const int Q = tq * 32 + r, c = tc * 32 + tx;
+    if (Q < F.X && c < RL) digits_f64(tile[tx][r], E, st, out + (long long)Q * RL + c, plane);
+  }
+}
+
+// One CTA per pair block (i <= j): reads T_ij from the double-float planes, writes the
+// digits of Tt and T for the (i,j) block and, if i != j, the (j,i) block, zeroes the
+// row padding, and stores the pair energy e_ij = sum_ab Tt_ij(a,b) T_ij(a,b) D_ijab.
+__global__ void __launch_bounds__(256)
+k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
+  __shared__ float Xh[32][33], Xl[32][33], Yh[32][33], Yl[32][33];
+  __shared__ float ebh[32], ebl[32];
+  __shared__ double red_h[8], red_l[8];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const long long gp = blockIdx.x;
+  const SplitFragDev& F = f[find_sfd(f, nf, gp, 2)];
+  int i, j;
+  tri_rc(gp - F.pair_begin, i, j);
+  const int v = F.v, o = F.o;
+  const long long ov = (long long)o * v;
+  const int RL = o * F.vpad;
+  char* ws = (char*)bs.ws;
+  const float* Th = (const float*)(ws + F.thi);
+  const float* Tl = (const float*)(ws + F.tlo);
+  const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
+  const int E_T = (int)emax - 124, E_Tt = (int)emax - 123;
+  __nv_bfloat16* tts = (__nv_bfloat16*)(ws + F.tts);
+  __nv_bfloat16* ts = (__nv_bfloat16*)(ws + F.ts);
+  const long long plane = ov * RL;
+  const double* eo = bs.eps + F.eo_off;
+  const double* ev = bs.eps + F.ev_off;
+  const double eij = eo[i] + eo[j];
+  const long long rowI = (long long)i * v, rowJ = (long long)j * v;
+  const int colI = i * F.vpad, colJ = j * F.vpad;
+  dfl e_acc = {0.f, 0.f};
+  const int nt = (v + 31) / 32;
+  const long long npairs = (long long)nt * (nt + 1) / 2;
+
+  auto put = [&](long long row, int col, dfl t, dfl tt) {
+    const long long o_ = row * RL + col;
+    digits_df(t, E_T, st, ts + o_, plane);
+    digits_df(tt, E_Tt, st, tts + o_, plane);
+  };
+
+  for (long long q = 0; q < npairs; ++q) {
+    int ta, tb;
+    tri_rc(q, ta, tb);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int l = ty + 8 * r;
+      const int a = ta * 32 + l, b = tb * 32 + tx;
+      const bool okx = a < v && b < v;
+      const long long ix = (rowI + a) * ov + rowJ + b;
+      Xh[l][tx] = okx ? Th[ix] : 0.f;
+      Xl[l][tx] = okx ? Tl[ix] : 0.f;
+      const int a2 = tb * 32 + l, b2 = ta * 32 + tx;
+      const bool oky = a2 < v && b2 < v;
+      const long long iy = (rowI + a2) * ov + rowJ + b2;
+      Yh[l][tx] = oky ? Th[iy] : 0.f;
+      Yl[l][tx] = oky ? Tl[iy] : 0.f;
+    }
+    if (ty == 0) {
+      const int b = tb * 32 + tx;
+      const dfl e = d_from(b < v ? ev[b] : 0.0);
+      ebh[tx] = e.h;
+      ebl[tx] = e.l;
+    }
+    __syncthreads();
+    // (i,j) block, tile (ta, tb): T = X[a][b], Tt = 2 X[a][b] - Y[b][a]
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int l = ty + 8 * r;
+      const int a = ta * 32 + l, b = tb * 32 + tx;
+      if (a < v && b < v) {
+        const dfl t = {Xh[l][tx], Xl[l][tx]};
+        const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Yh[tx][l], Yl[tx][l]}));
+        put(rowI + a, colJ + b, t, tt);
+        const dfl D = d_add(d_from(eij - ev[a]), d_neg({ebh[tx], ebl[tx]}));
+        e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
+      }
+    }
+    __syncthreads();
+    if (ta != tb) {
+      // the (tb, ta) tile needs e_b for b in ta
+      if (ty == 0) {
+        const int b = ta * 32 + tx;
+        const dfl e = d_from(b < v ? ev[b] : 0.0);
+        ebh[tx] = e.h;
+        ebl[tx] = e.l;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int l = ty + 8 * r;
+        const int a = tb * 32 + l, b = ta * 32 + tx;
+        if (a < v && b < v) {
+          const dfl t = {Yh[l][tx], Yl[l][tx]};
+          const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Xh[tx][l], Xl[tx][l]}));
+          put(rowI + a, colJ + b, t, tt);
+          const dfl D = d_add(d_from(eij - ev[a]), d_neg({ebh[tx], ebl[tx]}));
+          e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
+        }
+      }
+    }
+    if (i != j) {
+      // (j,i) block: T_ji(a',b') = T_ij(b',a'), Tt_ji(a',b') = Tt_ij(b',a')
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int l = ty + 8 * r;
+        const int ap = tb * 32 + l, bp = ta * 32 + tx;
+        if (ap < v && bp < v) {
+          const dfl t = {Xh[tx][l], Xl[tx][l]};
+          const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Yh[l][tx], Yl[l][tx]}));
+          put(rowJ + ap, colI + bp, t, tt);
+        }
+        if (ta != tb) {
+          const int ap2 = ta * 32 + l, bp2 = tb * 32 + tx;
+          if (ap2 < v && bp2 < v) {
+            const dfl t = {Yh[tx][l], Yl[tx][l]};
+            const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Xh[l][tx], Xl[l][tx]}));
+            put(rowJ + ap2, colI + bp2, t, tt);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // zero the padding columns b in [v, vpad) of this block's rows
+  const int npad = F.vpad - v;
+  if (npad > 0) {
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int e = tid; e < v * npad; e += blockDim.x) {
+      const int a = e / npad, b = v + e % npad;
+      for (int p = 0; p < st; ++p) {
+        tts[p * plane + (rowI + a) * RL + colJ + b] = z;
+        ts[p * plane + (rowI + a) * RL + colJ + b] = z;
+        if (i != j) {
+          tts[p * plane + (rowJ + a) * RL + colI + b] = z;
+          ts[p * plane + (rowJ + a) * RL + colI + b] = z;
+        }
+      }
+    }
+  }
+  // pair energy: warp, then block, in double-float; one FP64 value per pair
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const dfl o2 = {__shfl_down_sync(0xffffffffu, e_acc.h, off),
+                    __shfl_down_sync(0xffffffffu, e_acc.l, off)};
+    e_acc = d_add(e_acc, o2);
+  }
+  if (tx == 0) { red_h[ty] = e_acc.h; red_l[ty] = e_acc.l; }
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    for (int w = 0; w < 8; ++w) e += (double)red_h[w] + (double)red_l[w];
+    double* ep = (double*)(ws + F.ep);
+    ep[(long long)i * o + j] = e;
+    ep[(long long)j * o + i] = e;
+  }
+}
+
+// ------------------------------------------------------------------ host
+
 int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.precision = precision;
   sp.slices_v = opt.slices_v;
   sp.slices_t = opt.slices_t;
-  return RIMP2_ERR_UNSUPPORTED;
+  sp.cfg_v = split_launch_config(sp.slices_v);
+  sp.cfg_t = split_launch_config(sp.slices_t);
+  sp.grid = split_gemm_grid();
+  if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
+  sp.ready = true;
+  return RIMP2_OK;
 }
+
 void split_plan_release(SplitPlan&) {}
-size_t split_frag_ws_elems(const SplitPlan&, const rimp2_frag&) { return 0; }
-int split_build_wave(SplitPlan&, const rimp2_frag*, const std::vector<int>&,
-                     std::vector<FragDev>&, SplitWave&, long long&, long long&) {
-  return RIMP2_ERR_UNSUPPORTED;
+
+namespace {
+
+struct Layout {
+  size_t bs1, bs2, erow, drow, thi, tlo, tts, ts, ep, scal, total;
+};
+
+Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
+  const size_t o = f.nocc, v = f.nvir, X = f.naux;
+  const size_t ov = o * v, vpad = rup((int)v, 8), xpad = rup((int)X, 8), RL = o * vpad;
+  Layout L{};
+  size_t off = 0;
+  L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * 2);
+  L.bs2 = off; off += al256((size_t)sp.slices_t * X * RL * 2);
+  L.erow = off; off += al256(ov * 4);
+  L.drow = off; off += al256(ov * 8);
+  L.thi = off; off += al256(ov * ov * 4);
+  L.tlo = off; off += al256(ov * ov * 4);
+  L.tts = off; off += al256((size_t)sp.slices_t * ov * RL * 2);
+  L.ts = off; off += al256((size_t)sp.slices_t * ov * RL * 2);
+  L.ep = off; off += al256(o * o * 8);
+  L.scal = off; off += 256;
+  L.total = off;
+  return L;
 }
-size_t split_layout_wave(SplitWave& w, size_t off) { w.off = off; return off + w.bytes; }
-void split_fill_wave(const SplitWave& w, char* host_block) {
-  if (w.bytes) memcpy(host_block + w.off, w.host.data(), w.bytes);
+
+void choose_split_k(SplitProb& P, int grid) {
+  const long long tiles = (long long)P.tiles_m * P.tiles_n;
+  long long want = std::max(1LL, (2LL * grid + tiles - 1) / tiles);
+  want = std::min<long long>(want, std::max(1, P.k1_count));
+  int chunk = (int)((P.k1_count + want - 1) / want);
+  if (chunk < 1) chunk = 1;
+  P.k1_chunk = chunk;
+  P.ksplit = std::max(1, (P.k1_count + chunk - 1) / chunk);
 }
-int split_enqueue_wave(SplitPlan&, SplitWave&, char*, const FragDev*, int, long long, Bases,
-                       unsigned*, cudaStream_t, int*, long long*) {
-  return RIMP2_ERR_UNSUPPORTED;
+
+void finish(std::vector<SplitProb>& v, long long& total) {
+  std::stable_sort(v.begin(), v.end(), [](const SplitProb& a, const SplitProb& b) {
+    return (double)a.k0_blocks * a.k1_chunk > (double)b.k0_blocks * b.k1_chunk;
+  });
+  total = 0;
+  for (auto& P : v) {
+    P.tile_begin = total;
+    total += P.ntiles;
+  }
+}
+
+}  // namespace
+
+size_t split_frag_ws_bytes(const SplitPlan& sp, const rimp2_frag& f) {
+  return frag_layout(sp, f).total;
+}
+
+int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<int>& members,
+                     const double* B, void* ws, std::vector<FragDev>& fdev, SplitWave& w,
+                     long long& total_pairs, long long& max_b) {
+  (void)B;
+  char* wsb = (char*)ws;
+  size_t off = 0;
+  long long pairs = 0, rows = 0, b2t = 0;
+  const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max;
+  const int sv = sp.slices_v, st = sp.slices_t;
+  w.want_gamma = false;
+  for (int idx : members) {
+    const rimp2_frag& f = frags[idx];
+    const Layout L = frag_layout(sp, f);
+    const int o = f.nocc, v = f.nvir, X = f.naux;
+    const int ov = o * v, vpad = rup(v, 8), xpad = rup(X, 8), RL = o * vpad;
+    SplitFragDev s{};
+    s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
+    s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
+    s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
+    s.thi = off + L.thi; s.tlo = off + L.tlo; s.tts = off + L.tts; s.ts = off + L.ts;
+    s.ep = off + L.ep; s.scal = off + L.scal;
+    s.pair_begin = pairs; s.row_begin = rows; s.b2_tile_begin = b2t;
+    pairs += (long long)o * (o + 1) / 2;
+    rows += ov;
+    const bool g = f.gamma_off >= 0 && X > 0 && ov > 0;
+    if (g) {
+      b2t += (long long)((X + 31) / 32) * ((RL + 31) / 32);
+      w.want_gamma = true;
+    }
+    w.sfd.push_back(s);
+    // the shared FP64 kernels (checks, energy reduce, zeroing) use FragDev
+    FragDev d{};
+    d.o = o; d.v = v; d.X = X; d.idx = idx;
+    d.b_off = f.b_off; d.eo_off = f.eo_off; d.ev_off = f.ev_off;
+    d.t_off = d.tt_off = -1;
+    d.ep_off = (long long)(s.ep / 8);
+    d.gamma_off = f.gamma_off; d.pij_off = f.pij_off; d.pab_off = f.pab_off;
+    d.epair_off = f.epair_off; d.pair_begin = s.pair_begin;
+    fdev.push_back(d);
+    max_b = std::max<long long>(max_b, (long long)ov * X);
+    off += L.total;
+    if (ov == 0) continue;
+
+    // V over rows (i,a) x (j,b), K = Q
+    {
+      SplitProb P{};
+      P.kind = PK_V; P.frag = idx;
+      P.M = P.N = ov; P.n_tile = NTv;
+      P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (ov + NTv - 1) / NTv;
+      P.ksplit = 1; P.k0_blocks = (X + SG_BK - 1) / SG_BK; P.k1_count = 1; P.k1_chunk = 1;
+      P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
+      P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
+      P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ov; P.alpha = 1.0;
+      P.d_off = s.drow; P.et_off = s.scal + 4; P.v = v;
+      P.ntiles = (long long)P.tiles_m * P.tiles_n;
+      const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
+      const uint64_t str[2] = {(uint64_t)xpad * 2, (uint64_t)ov * xpad * 2};
+      const uint32_t boxA[3] = {SG_BK, SG_BM, 1}, boxB[3] = {SG_BK, (uint32_t)NTv, 1};
+      if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB) != RIMP2_OK)
+        return RIMP2_ERR_UNSUPPORTED;
+      w.probs_v.push_back(P);
+    }
+    const uint64_t plane_b = (uint64_t)ov * RL * 2;
+    if (g) {  // Gamma[(i,a)][Q] = sum_(j,b) Tt[(i,a)][(j,b)] B[(j,b)][Q]
+      SplitProb P{};
+      P.kind = PK_GAMMA; P.frag = idx;
+      P.M = ov; P.N = X; P.n_tile = NTt;
+      P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTt - 1) / NTt;
+      P.ksplit = 1; P.k0_blocks = (RL + SG_BK - 1) / SG_BK; P.k1_count = 1; P.k1_chunk = 1;
+      P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
+      P.ea_rows = P.eb_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
+      P.eb_off = s.scal; P.eb_add = 0;
+      P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
+      P.ntiles = (long long)P.tiles_m * P.tiles_n;
+      const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)st};
+      const uint64_t sA[2] = {(uint64_t)RL * 2, plane_b};
+      const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
+      const uint64_t sB[2] = {(uint64_t)RL * 2, (uint64_t)X * RL * 2};
+      const uint32_t boxA[3] = {SG_BK, SG_BM, 1}, boxB[3] = {SG_BK, (uint32_t)NTt, 1};
+      if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB) != RIMP2_OK)
+        return RIMP2_ERR_UNSUPPORTED;
+      w.probs_c.push_back(P);
+    }
+    if (f.pab_off >= 0) {  // P_ab = sum_i sum_(j,c) Tt[(i,a)][(j,c)] T[(i,b)][(j,c)]
+      SplitProb P{};
+      P.kind = PK_PAB; P.frag = idx;
+      P.M = P.N = v; P.n_tile = NTt;
+      P.tiles_m = (v + SG_BM - 1) / SG_BM; P.tiles_n = (v + NTt - 1) / NTt;
+      P.k0_blocks = (RL + SG_BK - 1) / SG_BK; P.k1_count = o;
+      P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
+      P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
+      P.ea_add = -123; P.eb_add = -124;
+      P.c_off = f.pab_off; P.ldc = v; P.alpha = 1.0;
+      choose_split_k(P, sp.grid);
+      P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
+      const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
+      const uint64_t s4[3] = {(uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
+      const uint32_t boxA[4] = {SG_BK, SG_BM, 1, 1}, boxB[4] = {SG_BK, (uint32_t)NTt, 1, 1};
+      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
+        return RIMP2_ERR_UNSUPPORTED;
+      w.probs_c.push_back(P);
+    }
+    if (f.pij_off >= 0) {  // P_ij = -sum_(k,a) sum_b Tt[(i,a)][(k,b)] T[(j,a)][(k,b)]
+      SplitProb P{};
+      P.kind = PK_PIJ; P.frag = idx;
+      P.M = P.N = o; P.n_tile = NTt;
+      P.tiles_m = (o + SG_BM - 1) / SG_BM; P.tiles_n = (o + NTt - 1) / NTt;
+      P.k0_blocks = (vpad + SG_BK - 1) / SG_BK; P.k1_count = o * v;
+      P.a_mode = P.b_mode = TM_5D; P.div5 = v;
+      P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
+      P.ea_add = -123; P.eb_add = -124;
+      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0;
+      choose_split_k(P, sp.grid);
+      P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
+      const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
+      const uint64_t s5[4] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
+      const uint32_t boxA[5] = {SG_BK, 1, 1, SG_BM, 1}, boxB[5] = {SG_BK, 1, 1, (uint32_t)NTt, 1};
+      if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB) != RIMP2_OK)
+        return RIMP2_ERR_UNSUPPORTED;
+      w.probs_c.push_back(P);
+    }
+  }
+  total_pairs = pairs;
+  w.rows = rows;
+  w.b2_tiles = b2t;
+  finish(w.probs_v, w.tiles_v);
+  finish(w.probs_c, w.tiles_c);
+  return RIMP2_OK;
+}
+
+size_t split_layout_wave(SplitWave& w, size_t off) {
+  off = al256(off);
+  w.off_sfd = off; off = al256(off + w.sfd.size() * sizeof(SplitFragDev));
+  w.off_pv = off; off = al256(off + w.probs_v.size() * sizeof(SplitProb));
+  w.off_pc = off; off = al256(off + w.probs_c.size() * sizeof(SplitProb));
+  return off;
+}
+
+void split_fill_wave(const SplitWave& w, char* host) {
+  if (!w.sfd.empty()) memcpy(host + w.off_sfd, w.sfd.data(), w.sfd.size() * sizeof(SplitFragDev));
+  if (!w.probs_v.empty()) memcpy(host + w.off_pv, w.probs_v.data(), w.probs_v.size() * sizeof(SplitProb));
+  if (!w.probs_c.empty()) memcpy(host + w.off_pc, w.probs_c.data(), w.probs_c.size() * sizeof(SplitProb));
+}
+
+int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* dfd, int nf,
+                       long long total_pairs, Bases bs, unsigned* ctr, cudaStream_t s,
+                       int* launches, long long* tiles, cudaEvent_t* ev) {
+  const SplitFragDev* sfd = (const SplitFragDev*)(dblk + w.off_sfd);
+  int nl = 0;
+  cudaError_t e = cudaSuccess;
+  k_split_reset<<<(nf + 127) / 128, 128, 0, s>>>(sfd, nf, bs);
+  ++nl;
+  e = cudaGetLastError();
+  if (e == cudaSuccess && w.rows > 0) {
+    k_slice_b1<<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
+    ++nl;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && w.b2_tiles > 0) {
+    k_slice_b2<<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    ++nl;
+    e = cudaGetLastError();
+  }
+  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  if (e == cudaSuccess && w.tiles_v > 0) {
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pv), (int)w.probs_v.size(), w.tiles_v, bs,
+                          ctr + 0, sp.cfg_v, sp.grid, s);
+    ++nl;
+  }
+  if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+  if (e == cudaSuccess && total_pairs > 0) {
+    k_amp_split<<<(unsigned)total_pairs, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    ++nl;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) { e = launch_energy_reduce(dfd, nf, bs, s); ++nl; }
+  if (e == cudaSuccess) { e = launch_zero_p(dfd, nf, bs, s); ++nl; }
+  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+  if (e == cudaSuccess && w.tiles_c > 0) {
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pc), (int)w.probs_c.size(), w.tiles_c, bs,
+                          ctr + 1, sp.cfg_t, sp.grid, s);
+    ++nl;
+  }
+  if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
+  *launches = nl;
+  *tiles = w.tiles_v + w.tiles_c;
+  return e == cudaSuccess ? RIMP2_OK : RIMP2_ERR_CUDA;
 }
 
 }  // namespace rimp2

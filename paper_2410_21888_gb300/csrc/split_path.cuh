@@ -5,30 +5,52 @@
 #include <vector>
 
 #include "rimp2_internal.cuh"
+#include "split_gemm.cuh"
 
 namespace rimp2 {
+
+// Per-fragment workspace layout of the split path (byte offsets into the workspace).
+struct SplitFragDev {
+  int o, v, X, idx;
+  int vpad, xpad, pad0, pad1;
+  long long b_off, eo_off, ev_off;  // elements into the B / eps pools
+  long long bs1;    // B digits for V: [s_v][o*v][xpad] bf16, per-row scale
+  long long bs2;    // B digits for Gamma: [s_t][X][o*vpad] bf16, one scale
+  long long erow;   // int32 [o*v] row exponents of bs1
+  long long drow;   // float2 [o*v]: e_i - e_a as a double-float
+  long long thi, tlo;  // float [o*v][o*v]: T as a double-float pair of planes
+  long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
+  long long ep;     // double [o][o] pair energies
+  long long scal;   // int32 [0]: exponent of the B (Gamma) scale; uint32 [1]: max |T| exponent
+  long long pair_begin, row_begin, b2_tile_begin;
+};
 
 struct SplitPlan {
   int precision = 0;
   int slices_v = 0, slices_t = 0;
+  SplitLaunch cfg_v{}, cfg_t{};
+  int grid = 0;
   bool ready = false;
 };
 
 struct SplitWave {
-  size_t off = 0, bytes = 0;
-  std::vector<char> host;  // descriptors copied into the plan's device block
+  std::vector<SplitFragDev> sfd;
+  std::vector<SplitProb> probs_v, probs_c;
+  long long tiles_v = 0, tiles_c = 0, rows = 0, b2_tiles = 0;
+  bool want_gamma = false;
+  size_t off_sfd = 0, off_pv = 0, off_pc = 0;  // byte offsets in the plan device block
 };
 
 int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt);
 void split_plan_release(SplitPlan& sp);
-size_t split_frag_ws_elems(const SplitPlan& sp, const rimp2_frag& f);
+size_t split_frag_ws_bytes(const SplitPlan& sp, const rimp2_frag& f);
 int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<int>& members,
-                     std::vector<FragDev>& fdev, SplitWave& w, long long& total_pairs,
-                     long long& max_b);
+                     const double* B, void* ws, std::vector<FragDev>& fdev, SplitWave& w,
+                     long long& total_pairs, long long& max_b);
 size_t split_layout_wave(SplitWave& w, size_t off);
 void split_fill_wave(const SplitWave& w, char* host_block);
 int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* dfd, int nf,
                        long long total_pairs, Bases bs, unsigned* ctr, cudaStream_t s,
-                       int* launches, long long* tiles);
+                       int* launches, long long* tiles, cudaEvent_t* ev);
 
 }  // namespace rimp2

@@ -58,7 +58,7 @@ class Batch(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("slices_v", ctypes.c_int32), ("slices_t", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("profile_stages", ctypes.c_int32),
                 ("max_workspace_bytes", ctypes.c_size_t)]
 
 
@@ -66,7 +66,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("flops_per_call", ctypes.c_double), ("last_ms", ctypes.c_double),
                 ("calls", ctypes.c_int64), ("tiles_per_call", ctypes.c_int64),
                 ("launches_per_call", ctypes.c_int32), ("waves", ctypes.c_int32),
-                ("graph_captures", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("graph_captures", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("stage_ms", ctypes.c_double * 4)]
 
 
 _lib = None
@@ -139,8 +140,8 @@ class Plan:
     """rimp2_plan for a fixed list of fragment shapes (nocc, nvir, naux)."""
 
     def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 5,
-                 slices_t: int = 5, use_graph: bool = True, check_inputs: bool = True,
-                 max_workspace_bytes: int = 0):
+                 slices_t: int = 6, use_graph: bool = True, check_inputs: bool = True,
+                 max_workspace_bytes: int = 0, profile_stages: bool = False):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -152,6 +153,7 @@ class Plan:
         opt.slices_v, opt.slices_t = int(slices_v), int(slices_t)
         opt.use_graph, opt.check_inputs = int(use_graph), int(check_inputs)
         opt.max_workspace_bytes = int(max_workspace_bytes)
+        opt.profile_stages = int(profile_stages)
         h = ctypes.c_void_p()
         _check(lib.rimp2_plan_create(frags, len(self.dims), PRECISIONS[precision],
                                      ctypes.byref(opt), ctypes.byref(h)), "rimp2_plan_create")

@@ -1,0 +1,146 @@
+"""GPU tests of the split-precision (BF16 integer-slice, tcgen05) path.
+
+1. The tensor-core slice GEMM alone against exact integer arithmetic: digits in
+   [-128, 128], level sums 2^(-8(p+q)) sum_k A_p B_q for p + q < s.  Levels 0..3 of each
+   256-long K chunk are exact integers in FP32; the chunks are combined in double-float,
+   so the result matches the exact value to ~2^-46 relative.
+2. Fragments through rimp2_energy_grad(precision=BF16_SPLIT) against the FP64 oracle.
+   Tolerances: energy within 1e-8 Eh per fragment; Gamma, P_ij, P_ab, pair energies
+   within 1e-9 relative Frobenius (the accuracy target of the split path).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2410_21888_gb300 import rimp2, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_E_ABS = 1e-8
+TOL_A = 1e-9
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def _hook():
+    lib = rimp2.load()
+    f = lib.rimp2_testing_slice_gemm
+    f.argtypes = [ctypes.c_int32] * 5 + [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    return f
+
+
+def _exact_levels(A, B, s, chunk=256):
+    """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the sum over
+    256-long K chunks of |chunk level sums| (the magnitudes the kernel accumulates)."""
+    M, N, K = A.shape[1], B.shape[1], A.shape[2]
+    out = np.zeros((M, N))
+    mag = np.zeros((M, N))
+    for k0 in range(0, max(K, 1), chunk):
+        for l in range(s):
+            lev = np.zeros((M, N), dtype=np.int64)
+            for p in range(l + 1):
+                q = l - p
+                lev += A[p, :, k0:k0 + chunk].astype(np.int64) @ B[q, :, k0:k0 + chunk].astype(np.int64).T
+            out += lev.astype(np.float64) * 2.0 ** (-8 * l)
+            mag += np.abs(lev).astype(np.float64) * 2.0 ** (-8 * l)
+    return out, mag
+
+
+@pytest.mark.parametrize("M,N,K,s,seed", [
+    (128, 96, 64, 2, 0),
+    (128, 96, 32, 5, 1),
+    (200, 150, 300, 5, 2),       # ragged M/N, two 256-chunks with a tail
+    (130, 97, 1000, 3, 3),       # four chunks
+    (64, 40, 33, 4, 4),          # partial tiles and a partial K block
+    (300, 260, 700, 6, 5),       # n_tile 80
+    (129, 70, 257, 8, 6),        # n_tile 64, eight slices
+])
+def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
+    rng = np.random.default_rng(seed)
+    kpad = (K + 7) // 8 * 8
+    A = rng.integers(-128, 129, size=(s, M, K))
+    B = rng.integers(-128, 129, size=(s, N, K))
+    if seed == 0:                       # worst case for exactness: all products 2^14
+        A[:] = 128
+        B[:] = -128
+    Ap = np.zeros((s, M, kpad)); Ap[:, :, :K] = A
+    Bp = np.zeros((s, N, kpad)); Bp[:, :, :K] = B
+    Ad = torch.tensor(Ap, dtype=torch.bfloat16, device="cuda")
+    Bd = torch.tensor(Bp, dtype=torch.bfloat16, device="cuda")
+    assert torch.equal(Ad.float().cpu(), torch.tensor(Ap, dtype=torch.float32))
+    C = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
+    rc = _hook()(M, N, K, kpad, s, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+                 torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    ref, mag = _exact_levels(A, B, s)
+    got = C.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    # an FP32 accumulator alone would give 2^-24, a wrong digit product at least 2^-14
+    # of the level-0 magnitude; demand double-float accuracy: 2^-44 of the chunk sums
+    bound = 2.0 ** -44 * (mag + 1.0)
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
+
+
+def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
+    E = float(out["energy"].item())
+    assert abs(E - ref["energy"]) <= tol_e, (E, ref["energy"], E - ref["energy"])
+    for k in ("gamma", "pij", "pab", "epair"):
+        g = out[k].detach().cpu().numpy()
+        assert rel(g, ref[k]) <= tol_a, (k, rel(g, ref[k]))
+
+
+@pytest.mark.parametrize("dims,seed", [
+    ((10, 40, 150), 0),
+    ((3, 5, 7), 2),
+    ((2, 70, 33), 3),
+    ((7, 13, 129), 4),
+    ((13, 37, 17), 6),
+    ((1, 1, 1), 1),
+    ((5, 31, 1), 5),
+    ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
+])
+def test_split_fragment_parity(dims, seed):
+    f = synth.fragment_inputs(*dims, seed=seed)
+    ref = oracle.fragment(f.B, f.eo, f.ev)
+    out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16")
+    check_split(out, ref)
+
+
+def test_split_degenerate_sizes():
+    for dims in [(3, 0, 5), (0, 4, 5), (3, 4, 0)]:
+        f = synth.fragment_inputs(*dims, seed=0)
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16")
+        assert float(out["energy"].item()) == 0.0
+        for k in ("gamma", "pij", "pab"):
+            assert torch.count_nonzero(out[k]).item() == 0
+
+
+def test_split_uneven_batch_matches_oracle():
+    s = synth.MonomerSystem(n_monomers=6, box=14.0, seed=0, nocc_range=(2, 5))
+    polys = [(0,), (3,), (0, 1), (2, 4), (1, 3, 5), (0, 2, 4), (5,)]
+    frags = [s.fragment(p) for p in polys]
+    eng = rimp2.Engine([f.B.shape for f in frags], precision="bf16")
+    eng.set_inputs(frags)
+    eng.run()
+    torch.cuda.synchronize()
+    eng.check_status()
+    for k, f in enumerate(frags):
+        check_split(eng.views(k), oracle.fragment(f.B, f.eo, f.ev))
+
+
+def test_split_error_decreases_with_slices():
+    f = synth.fragment_inputs(6, 30, 90, seed=11)
+    ref = oracle.fragment(f.B, f.eo, f.ev)
+    errs = []
+    for s in (3, 4, 6):
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", slices_v=s, slices_t=s)
+        errs.append(rel(out["gamma"].cpu().numpy(), ref["gamma"]))
+    assert errs[0] > errs[1] > errs[2] or errs[2] < 1e-12, errs
