@@ -187,7 +187,9 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 __global__ void __launch_bounds__(256)
 k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   __shared__ float Xh[32][33], Xl[32][33], Yh[32][33], Yl[32][33];
-  __shared__ float ebh[32], ebl[32];
+  // per tile pair: r_a = (e_i + e_j) - e_a for rows and e_b for columns, as double-floats
+  // (formed once per row/column in FP64, so the inner loops stay in FP32)
+  __shared__ float Rta[2][32], Rtb[2][32], Eta[2][32], Etb[2][32];
   __shared__ double red_h[8], red_l[8];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const long long gp = blockIdx.x;
@@ -237,11 +239,15 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       Yh[l][tx] = oky ? Th[iy] : 0.f;
       Yl[l][tx] = oky ? Tl[iy] : 0.f;
     }
-    if (ty == 0) {
-      const int b = tb * 32 + tx;
-      const dfl e = d_from(b < v ? ev[b] : 0.0);
-      ebh[tx] = e.h;
-      ebl[tx] = e.l;
+    if (ty < 2) {
+      const int t = ty == 0 ? ta : tb;
+      const int k = t * 32 + tx;
+      const dfl r = d_from(k < v ? eij - ev[k] : 0.0);
+      const dfl e = d_from(k < v ? ev[k] : 0.0);
+      float (*R)[32] = ty == 0 ? Rta : Rtb;
+      float (*Ev)[32] = ty == 0 ? Eta : Etb;
+      R[0][tx] = r.h; R[1][tx] = r.l;
+      Ev[0][tx] = e.h; Ev[1][tx] = e.l;
     }
     __syncthreads();
     // (i,j) block, tile (ta, tb): T = X[a][b], Tt = 2 X[a][b] - Y[b][a]
@@ -253,20 +259,11 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
         const dfl t = {Xh[l][tx], Xl[l][tx]};
         const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Yh[tx][l], Yl[tx][l]}));
         put(rowI + a, colJ + b, t, tt);
-        const dfl D = d_add(d_from(eij - ev[a]), d_neg({ebh[tx], ebl[tx]}));
+        const dfl D = d_add({Rta[0][l], Rta[1][l]}, d_neg({Etb[0][tx], Etb[1][tx]}));
         e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
       }
     }
-    __syncthreads();
     if (ta != tb) {
-      // the (tb, ta) tile needs e_b for b in ta
-      if (ty == 0) {
-        const int b = ta * 32 + tx;
-        const dfl e = d_from(b < v ? ev[b] : 0.0);
-        ebh[tx] = e.h;
-        ebl[tx] = e.l;
-      }
-      __syncthreads();
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int l = ty + 8 * r;
@@ -275,7 +272,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
           const dfl t = {Yh[l][tx], Yl[l][tx]};
           const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Xh[tx][l], Xl[tx][l]}));
           put(rowI + a, colJ + b, t, tt);
-          const dfl D = d_add(d_from(eij - ev[a]), d_neg({ebh[tx], ebl[tx]}));
+          const dfl D = d_add({Rtb[0][l], Rtb[1][l]}, d_neg({Eta[0][tx], Eta[1][tx]}));
           e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
         }
       }
