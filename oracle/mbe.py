@@ -33,3 +33,23 @@ def mbe3(E, monomers, dimers, trimers):
 def all_polymers(n):
     mons = list(range(n))
     return mons, list(itertools.combinations(mons, 2)), list(itertools.combinations(mons, 3))
+
+
+def polymers(centroids, r_dimer, r_trimer, rule="max"):
+    """Brute-force polymer lists: dimers with centroid distance <= r_dimer; trimers with
+    all pair distances <= r_trimer ("max") or at least two of them ("two_pairs")."""
+    import numpy as np
+    c = np.asarray(centroids, dtype=float)
+    n = len(c)
+
+    def d(a, b):
+        return float(np.sqrt(np.sum((c[a] - c[b]) ** 2)))
+
+    dimers = [(a, b) for a, b in itertools.combinations(range(n), 2) if d(a, b) <= r_dimer]
+    trimers = []
+    for a, b, e in itertools.combinations(range(n), 3):
+        ds = [d(a, b), d(a, e), d(b, e)]
+        ok = max(ds) <= r_trimer if rule == "max" else sum(x <= r_trimer for x in ds) >= 2
+        if ok:
+            trimers.append((a, b, e))
+    return dimers, trimers

@@ -303,3 +303,77 @@ def energy_grad(B, eo, ev, precision: str = "fp64", want_gamma=True, want_p=True
         eng.check_status()
     out["engine"] = eng
     return out
+
+
+# ---------------------------------------------------------------- MBE3 (include/rimp2_mbe.h)
+
+TRIMER_RULES = {"max": 0, "two_pairs": 1}
+
+
+def _mbe_lib():
+    lib = load()
+    if not getattr(lib, "_mbe_ready", False):
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.rimp2_mbe_polymers.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                           i32p, ctypes.c_int64, i64p, i32p, ctypes.c_int64, i64p]
+        lib.rimp2_mbe_polymers.restype = ctypes.c_int
+        lib.rimp2_mbe_coefficients.argtypes = [ctypes.c_int32, i32p, ctypes.c_int64, i32p,
+                                               ctypes.c_int64, i32p, i32p, ctypes.c_int64, i64p]
+        lib.rimp2_mbe_coefficients.restype = ctypes.c_int
+        lib.rimp2_mbe_combine.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+        lib.rimp2_mbe_combine.restype = ctypes.c_int
+        lib._mbe_ready = True
+    return lib
+
+
+def _i32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def mbe_polymers(centroids, r_dimer: float, r_trimer: float, rule: str = "max"):
+    """Dimers (n_d x 2) and trimers (n_t x 3) within the cutoffs (host, C++)."""
+    lib = _mbe_lib()
+    c = np.ascontiguousarray(centroids, dtype=np.float64)
+    n = c.shape[0]
+    nd, nt = ctypes.c_int64(), ctypes.c_int64()
+    cp = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib.rimp2_mbe_polymers(cp, n, r_dimer, r_trimer, TRIMER_RULES[rule], None, 0,
+                                  ctypes.byref(nd), None, 0, ctypes.byref(nt)),
+           "rimp2_mbe_polymers")
+    d = np.zeros((max(nd.value, 1), 2), dtype=np.int32)
+    t = np.zeros((max(nt.value, 1), 3), dtype=np.int32)
+    _check(lib.rimp2_mbe_polymers(cp, n, r_dimer, r_trimer, TRIMER_RULES[rule], _i32(d),
+                                  nd.value, ctypes.byref(nd), _i32(t), nt.value, ctypes.byref(nt)),
+           "rimp2_mbe_polymers")
+    return d[:nd.value], t[:nt.value]
+
+
+def mbe_coefficients(n: int, dimers, trimers):
+    """Fragments ([k] tuples of monomer ids) and integer coefficients c with
+    E_MBE3 = sum c_f E_f (host, C++)."""
+    lib = _mbe_lib()
+    d = np.ascontiguousarray(np.asarray(dimers, dtype=np.int32).reshape(-1, 2))
+    t = np.ascontiguousarray(np.asarray(trimers, dtype=np.int32).reshape(-1, 3))
+    nf = ctypes.c_int64()
+    _check(lib.rimp2_mbe_coefficients(n, _i32(d), len(d), _i32(t), len(t), None, None, 0,
+                                      ctypes.byref(nf)), "rimp2_mbe_coefficients")
+    fr = np.zeros((max(nf.value, 1), 3), dtype=np.int32)
+    co = np.zeros(max(nf.value, 1), dtype=np.int32)
+    _check(lib.rimp2_mbe_coefficients(n, _i32(d), len(d), _i32(t), len(t), _i32(fr), _i32(co),
+                                      nf.value, ctypes.byref(nf)), "rimp2_mbe_coefficients")
+    frags = [tuple(int(x) for x in row if x >= 0) for row in fr[:nf.value]]
+    return frags, co[:nf.value].copy()
+
+
+def mbe_combine(energy: torch.Tensor, coeff: torch.Tensor, stream=None) -> torch.Tensor:
+    """Device FP64 sum_f coeff[f] * energy[f] (compensated); returns a 1-element tensor."""
+    _require_cuda()
+    assert energy.dtype == torch.float64 and coeff.dtype == torch.int32
+    out = torch.empty(1, dtype=torch.float64, device=energy.device)
+    _check(_mbe_lib().rimp2_mbe_combine(energy.data_ptr(), coeff.data_ptr(), energy.numel(),
+                                        out.data_ptr(), _stream_handle(stream)),
+           "rimp2_mbe_combine")
+    return out
