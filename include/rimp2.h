@@ -126,8 +126,11 @@ typedef struct rimp2_plan rimp2_plan;
 /* Fills *opt with the defaults listed above. */
 void rimp2_default_options(rimp2_options* opt);
 
-/* Creates a plan for nfrag fragments with the given shapes (offsets are ignored here)
- * and precision.  opt may be NULL (defaults).  Allocates the plan's small device block
+/* Creates a plan for nfrag fragments with the given shapes and precision.  Offsets are
+ * ignored here except for the "not requested" markers: gamma_off, pij_off or pab_off
+ * = -1 at plan creation sizes the workspace without that output (an energy-only plan
+ * needs no Tt and no digit planes), and later calls may not request it
+ * (RIMP2_ERR_SHAPE).  opt may be NULL (defaults).  Allocates the plan's small device block
  * on the current device.  Returns RIMP2_ERR_BAD_ARG for null/negative inputs,
  * RIMP2_ERR_UNSUPPORTED for an unknown precision or slice count. */
 int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,

@@ -48,6 +48,14 @@ int rimp2_mbe_coefficients(int32_t n, const int32_t* dimers, int64_t nd, const i
 int rimp2_mbe_combine(const double* energy, const int32_t* coeff, int64_t nfrag, double* out,
                       void* stream);
 
+/* Device: per-polymer corrections out[t] = sum_q sign[q] * energy[terms[t][q]] for
+ * q < k (e.g. k = 3, signs {+1,-1,-1}, terms {IJ, I, J} for dimers; k = 7, signs
+ * {+1,-1,-1,-1,+1,+1,+1}, terms {IJK, IJ, IK, JK, I, J, K} for trimers), in FP64.
+ * terms [n][k] int32 (device), sign [k] int32 (device).  If out_log10 is not NULL it
+ * also receives log10(|out[t]| + 1e-16) as FP32 (the screen's regression target). */
+int rimp2_mbe_corrections(const double* energy, const int32_t* terms, const int32_t* sign,
+                          int64_t n, int32_t k, double* out, float* out_log10, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -190,7 +190,7 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
   const int v = F.v, o = F.o;
   const long long ov = (long long)o * v;
   const double* __restrict__ T = bs.ws + F.t_off;
-  double* __restrict__ Tt = bs.ws + F.tt_off;
+  double* __restrict__ Tt = bs.ws + (F.tt_off >= 0 ? F.tt_off : 0);   // unused if < 0
   const double* eo = bs.eps + F.eo_off;
   const double* ev = bs.eps + F.ev_off;
   const double eij = eo[i] + eo[j];
@@ -220,7 +220,7 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
       if (a < v && b < v) {
         const double t = X[l][tx];
         const double tt = 2.0 * t - Y[tx][l];
-        Tt[(rowI + a) * ov + rowJ + b] = tt;
+        if (F.tt_off >= 0) Tt[(rowI + a) * ov + rowJ + b] = tt;
         const double D = eij - ev[a] - ev[b];
         e_part += tt * (t * D);
       }
@@ -229,13 +229,13 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
         if (a2 < v && b2 < v) {
           const double t = Y[l][tx];
           const double tt = 2.0 * t - X[tx][l];
-          Tt[(rowI + a2) * ov + rowJ + b2] = tt;
+          if (F.tt_off >= 0) Tt[(rowI + a2) * ov + rowJ + b2] = tt;
           const double D = eij - ev[a2] - ev[b2];
           e_part += tt * (t * D);
         }
       }
     }
-    if (i != j) {
+    if (i != j && F.tt_off >= 0) {
       // (j,i) block: Tt_ji(a',b') = Tt_ij(b',a'); rows a' from tb, cols b' from ta
 #pragma unroll
       for (int r = 0; r < 4; ++r) {

@@ -51,7 +51,29 @@ k_mbe_combine(const double* __restrict__ E, const int* __restrict__ c, long long
   if (threadIdx.x == 0) *out = ss[0] + cc[0];
 }
 
+__global__ void k_mbe_corrections(const double* __restrict__ E, const int* __restrict__ terms,
+                                  const int* __restrict__ sign, long long n, int k, double* out,
+                                  float* out_log) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double s = 0.0;
+  for (int q = 0; q < k; ++q) s += (double)sign[q] * E[terms[t * k + q]];
+  out[t] = s;
+  if (out_log) out_log[t] = (float)log10(fabs(s) + 1e-16);
+}
+
 }  // namespace
+
+extern "C" int rimp2_mbe_corrections(const double* energy, const int32_t* terms,
+                                     const int32_t* sign, int64_t n, int32_t k, double* out,
+                                     float* out_log10, void* stream) {
+  if (n < 0 || k <= 0 || k > 16 || (n > 0 && (!energy || !terms || !sign || !out)))
+    return RIMP2_ERR_BAD_ARG;
+  if (n == 0) return RIMP2_OK;
+  k_mbe_corrections<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      energy, terms, sign, n, k, out, out_log10);
+  return cudaGetLastError() == cudaSuccess ? RIMP2_OK : RIMP2_ERR_CUDA;
+}
 
 extern "C" int rimp2_mbe_polymers(const double* c, int32_t n, double r_dimer, double r_trimer,
                                   int32_t rule, int32_t* dimers, int64_t cap_d, int64_t* n_dimers,

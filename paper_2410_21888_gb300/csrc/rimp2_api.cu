@@ -108,9 +108,12 @@ void rimp2_default_options(rimp2_options* opt) {
 
 namespace {
 
+bool wants_tt(const rimp2_frag& f) { return f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0; }
+
 size_t frag_ws_elems_fp64(const rimp2_frag& f) {
   const size_t ov = (size_t)f.nocc * f.nvir;
-  return align_up(ov * ov, kAlignElems) * 2 + align_up((size_t)f.nocc * f.nocc, kAlignElems);
+  return align_up(ov * ov, kAlignElems) * (wants_tt(f) ? 2 : 1) +
+         align_up((size_t)f.nocc * f.nocc, kAlignElems);
 }
 
 size_t frag_ws_elems(const rimp2_plan* p, const rimp2_frag& f) {
@@ -163,7 +166,8 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
     d.b_off = f.b_off; d.eo_off = f.eo_off; d.ev_off = f.ev_off;
     const size_t ov = (size_t)f.nocc * f.nvir;
     d.t_off = (long long)ws; ws += align_up(ov * ov, kAlignElems);
-    d.tt_off = (long long)ws; ws += align_up(ov * ov, kAlignElems);
+    d.tt_off = -1;
+    if (wants_tt(f)) { d.tt_off = (long long)ws; ws += align_up(ov * ov, kAlignElems); }
     d.ep_off = (long long)ws; ws += align_up((size_t)f.nocc * f.nocc, kAlignElems);
     d.gamma_off = f.gamma_off; d.pij_off = f.pij_off; d.pab_off = f.pab_off;
     d.epair_off = f.epair_off;
@@ -435,6 +439,9 @@ int rimp2_energy_grad(rimp2_plan* p, const rimp2_batch* b, void* workspace, size
     const rimp2_frag& x = b->frags[f];
     const rimp2_frag& y = p->frags[f];
     if (x.nocc != y.nocc || x.nvir != y.nvir || x.naux != y.naux) return RIMP2_ERR_SHAPE;
+    if ((x.gamma_off >= 0 && y.gamma_off < 0) || (x.pij_off >= 0 && y.pij_off < 0) ||
+        (x.pab_off >= 0 && y.pab_off < 0))
+      return RIMP2_ERR_SHAPE;
     if (x.b_off < 0 || x.eo_off < 0 || x.ev_off < 0) return RIMP2_ERR_BAD_ARG;
     if ((x.gamma_off >= 0 && !b->gamma) || (x.pij_off >= 0 && !b->pij) ||
         (x.pab_off >= 0 && !b->pab) || (x.epair_off >= 0 && !b->epair))

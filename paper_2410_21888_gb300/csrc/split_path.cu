@@ -199,6 +199,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const int v = F.v, o = F.o;
   const long long ov = (long long)o * v;
   const int RL = o * F.vpad;
+  st = F.st_out;           // 0: energy only, no digit planes for this fragment
   char* ws = (char*)bs.ws;
   const float* Th = (const float*)(ws + F.thi);
   const float* Tl = (const float*)(ws + F.tlo);
@@ -359,16 +360,20 @@ struct Layout {
 Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   const size_t o = f.nocc, v = f.nvir, X = f.naux;
   const size_t ov = o * v, vpad = rup((int)v, 8), xpad = rup((int)X, 8), RL = o * vpad;
+  // digit planes of T / Tt (and B for Gamma) exist only when an output needs them
+  const bool want_t = f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0;
+  const size_t st_t = want_t ? (size_t)sp.slices_t : 0;
+  const size_t st_g = f.gamma_off >= 0 ? (size_t)sp.slices_t : 0;
   Layout L{};
   size_t off = 0;
   L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * 2);
-  L.bs2 = off; off += al256((size_t)sp.slices_t * X * RL * 2);
+  L.bs2 = off; off += al256(st_g * X * RL * 2);
   L.erow = off; off += al256(ov * 4);
   L.drow = off; off += al256(ov * 8);
   L.thi = off; off += al256(ov * ov * 4);
   L.tlo = off; off += al256(ov * ov * 4);
-  L.tts = off; off += al256((size_t)sp.slices_t * ov * RL * 2);
-  L.ts = off; off += al256((size_t)sp.slices_t * ov * RL * 2);
+  L.tts = off; off += al256(st_t * ov * RL * 2);
+  L.ts = off; off += al256(st_t * ov * RL * 2);
   L.ep = off; off += al256(o * o * 8);
   L.scal = off; off += 256;
   L.total = off;
@@ -419,6 +424,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     const int ov = o * v, vpad = rup(v, 8), xpad = rup(X, 8), RL = o * vpad;
     SplitFragDev s{};
     s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
+    s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
     s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
     s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
     s.thi = off + L.thi; s.tlo = off + L.tlo; s.tts = off + L.tts; s.ts = off + L.ts;

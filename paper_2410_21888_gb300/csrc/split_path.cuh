@@ -12,7 +12,7 @@ namespace rimp2 {
 // Per-fragment workspace layout of the split path (byte offsets into the workspace).
 struct SplitFragDev {
   int o, v, X, idx;
-  int vpad, xpad, pad0, pad1;
+  int vpad, xpad, st_out, pad1;   // st_out: T/Tt digit slices to write (0: energy only)
   long long b_off, eo_off, ev_off;  // elements into the B / eps pools
   long long bs1;    // B digits for V: [s_v][o*v][xpad] bf16, per-row scale
   long long bs2;    // B digits for Gamma: [s_t][X][o*vpad] bf16, one scale

@@ -141,7 +141,8 @@ class Plan:
 
     def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 5,
                  slices_t: int = 6, use_graph: bool = True, check_inputs: bool = True,
-                 max_workspace_bytes: int = 0, profile_stages: bool = False):
+                 max_workspace_bytes: int = 0, profile_stages: bool = False,
+                 want_gamma: bool = True, want_p: bool = True):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -149,6 +150,8 @@ class Plan:
         frags = (Frag * max(1, len(self.dims)))()
         for k, (o, v, X) in enumerate(self.dims):
             frags[k].nocc, frags[k].nvir, frags[k].naux = o, v, X
+            frags[k].gamma_off = 0 if want_gamma else -1
+            frags[k].pij_off = frags[k].pab_off = 0 if want_p else -1
         opt = default_options()
         opt.slices_v, opt.slices_t = int(slices_v), int(slices_t)
         opt.use_graph, opt.check_inputs = int(use_graph), int(check_inputs)
@@ -207,7 +210,8 @@ class Engine:
         _require_cuda()
         self.dims = [tuple(int(x) for x in d) for d in dims]
         self.device = torch.device(device)
-        self.plan = Plan(self.dims, precision=precision, **plan_opts)
+        self.plan = Plan(self.dims, precision=precision, want_gamma=want_gamma, want_p=want_p,
+                         **plan_opts)
         nb = sum(o * v * X for o, v, X in self.dims)
         ne = sum(o + v for o, v, X in self.dims)
         npij = sum(o * o for o, v, X in self.dims)
@@ -376,4 +380,82 @@ def mbe_combine(energy: torch.Tensor, coeff: torch.Tensor, stream=None) -> torch
     _check(_mbe_lib().rimp2_mbe_combine(energy.data_ptr(), coeff.data_ptr(), energy.numel(),
                                         out.data_ptr(), _stream_handle(stream)),
            "rimp2_mbe_combine")
+    return out
+
+
+def mbe_corrections(energy: torch.Tensor, terms: torch.Tensor, sign, want_log=False,
+                    stream=None):
+    """Device per-polymer corrections sum_q sign[q] E[terms[t, q]] (FP64) and optionally
+    log10(|.| + 1e-16) (FP32)."""
+    lib = _mbe_lib()
+    if not getattr(lib, "_corr_ready", False):
+        lib.rimp2_mbe_corrections.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64,
+                                              ctypes.c_int32] + [ctypes.c_void_p] * 3
+        lib.rimp2_mbe_corrections.restype = ctypes.c_int
+        lib._corr_ready = True
+    terms = terms.to(device="cuda", dtype=torch.int32).contiguous()
+    n, k = terms.shape
+    sg = torch.as_tensor(sign, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    lg = torch.empty(n, dtype=torch.float32, device="cuda") if want_log else None
+    _check(lib.rimp2_mbe_corrections(energy.data_ptr(), terms.data_ptr(), sg.data_ptr(), n, k,
+                                     out.data_ptr(), lg.data_ptr() if want_log else None,
+                                     _stream_handle(stream)), "rimp2_mbe_corrections")
+    return (out, lg) if want_log else out
+
+
+# ---------------------------------------------------------------- MLP screen (include/rimp2_mlp.h)
+
+MLP_PARAMS = 64 * 9 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _mlp_lib():
+    lib = load()
+    if not getattr(lib, "_mlp_ready", False):
+        vp = ctypes.c_void_p
+        lib.rimp2_screen_features.argtypes = [vp, vp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp]
+        lib.rimp2_screen_features.restype = ctypes.c_int
+        lib.rimp2_mlp_grad.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp]
+        lib.rimp2_mlp_grad.restype = ctypes.c_int
+        lib.rimp2_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp]
+        lib.rimp2_mlp_adam.restype = ctypes.c_int
+        lib.rimp2_mlp_predict.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp]
+        lib.rimp2_mlp_predict.restype = ctypes.c_int
+        lib._mlp_ready = True
+    return lib
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def screen_features(centroids, nocc, trimers, dimer_de, stream=None) -> torch.Tensor:
+    """[nt, 9] FP32 features (device) from device tensors: centroids [n,3] f64, nocc [n]
+    i32, trimers [nt,3] i32, dimer_de [n,n] f64."""
+    nt = trimers.shape[0]
+    out = torch.empty((nt, 9), dtype=torch.float32, device="cuda")
+    _check(_mlp_lib().rimp2_screen_features(_p(centroids), _p(nocc), centroids.shape[0],
+                                            _p(trimers), nt, _p(dimer_de), _p(out),
+                                            _stream_handle(stream)), "rimp2_screen_features")
+    return out
+
+
+def mlp_grad(master, feats, y, idx, n, mean, std, want_loss=True, stream=None):
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda") if want_loss else None
+    _check(_mlp_lib().rimp2_mlp_grad(_p(master), _p(feats), _p(y), _p(idx), int(n), _p(mean),
+                                     _p(std), _p(grad), _p(loss), _stream_handle(stream)),
+           "rimp2_mlp_grad")
+    return grad, loss
+
+
+def mlp_adam(master, grad, m, v, t, lr, stream=None):
+    _check(_mlp_lib().rimp2_mlp_adam(_p(master), _p(grad), _p(m), _p(v), int(t), float(lr),
+                                     _stream_handle(stream)), "rimp2_mlp_adam")
+
+
+def mlp_predict(master, feats, mean, std, stream=None) -> torch.Tensor:
+    out = torch.empty(feats.shape[0], dtype=torch.float32, device="cuda")
+    _check(_mlp_lib().rimp2_mlp_predict(_p(master), _p(feats), feats.shape[0], _p(mean), _p(std),
+                                        _p(out), _stream_handle(stream)), "rimp2_mlp_predict")
     return out

@@ -1,0 +1,248 @@
+"""Learned trimer screen: an MLP (include/rimp2_mlp.h) trained on trimer corrections
+dE_IJK that the engine itself computed predicts log10|dE_IJK| for candidate trimers;
+trimers predicted below a threshold are skipped, a random sample of the skipped ones is
+recomputed by the plain method as the judge, and the plain method stays the fallback
+(screen=None).
+
+Host code here is bookkeeping (polymer lists, index tables, minibatch permutations);
+features, labels, gradients, optimiser steps and predictions run in library kernels.
+"""
+from __future__ import annotations
+
+import time
+import zlib
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import rimp2
+
+TRIMER_SIGNS = (1, -1, -1, -1, 1, 1, 1)
+DIMER_SIGNS = (1, -1, -1)
+
+
+class DeviceBlockInputs:
+    """Fragment inputs restricted from one global B, with each (occ-owner, vir-owner,
+    aux-owner) block drawn on the GPU from its own seed, so every fragment containing a
+    block sees the same values (MBE differences cancel exactly as on the host
+    generator).  Same distribution and block scaling as synth.MonomerSystem."""
+
+    def __init__(self, system):
+        self.s = system
+        self.gen = torch.Generator(device="cuda")
+
+    def _seed(self, I, J, K):
+        return zlib.crc32(np.array([self.s.seed, 97, I, J, K], dtype=np.int64).tobytes())
+
+    def fill(self, eng, frags):
+        s = self.s
+        for k, f in enumerate(frags):
+            o, v, X = eng.dims[k]
+            b, e, _, _ = eng.offsets[k]
+            Bf = eng.B[b:b + o * v * X].view(o, v, X)
+            m = list(f)
+            oo = np.concatenate([[0], np.cumsum(s.nocc[m])])
+            vo = np.concatenate([[0], np.cumsum(s.nvir[m])])
+            xo = np.concatenate([[0], np.cumsum(s.naux[m])])
+            for p, I in enumerate(m):
+                for q, J in enumerate(m):
+                    for r, K in enumerate(m):
+                        self.gen.manual_seed(self._seed(I, J, K))
+                        blk = Bf[oo[p]:oo[p + 1], vo[q]:vo[q + 1], xo[r]:xo[r + 1]]
+                        blk.normal_(0.0, s.sigma, generator=self.gen)
+                        sc = s.block_scale((I, J, K))
+                        if sc != 1.0:
+                            blk.mul_(sc)
+            eo = np.concatenate([s.eps(I)[0] for I in m])
+            ev = np.concatenate([s.eps(I)[1] for I in m])
+            eng.eps[e:e + o].copy_(torch.from_numpy(eo))
+            eng.eps[e + o:e + o + v].copy_(torch.from_numpy(ev))
+
+
+def fragment_energies(system, frags, precision="bf16", slices_v=8, device_inputs=True,
+                      chunk_bytes=48 << 30, ws_budget=64 << 30):
+    """Energies of `frags` (tuples of monomer ids), energy only, one plan per chunk of
+    same-order fragments; returns (device FP64 tensor, seconds of GPU work)."""
+    out = torch.zeros(len(frags), dtype=torch.float64, device="cuda")
+    filler = DeviceBlockInputs(system) if device_inputs else None
+    gpu_s = 0.0
+    order = sorted(range(len(frags)), key=lambda k: (len(frags[k]), frags[k]))
+    chunk, bytes_ = [], 0
+    pending = []
+
+    def flush(idx):
+        nonlocal gpu_s
+        if not idx:
+            return
+        fl = [frags[k] for k in idx]
+        eng = rimp2.Engine([system.fragment_dims(f) for f in fl], precision=precision,
+                           want_gamma=False, want_p=False, want_epair=False,
+                           max_workspace_bytes=ws_budget, slices_v=slices_v)
+        if filler is not None:
+            filler.fill(eng, fl)
+        else:
+            eng.set_inputs([system.fragment(f) for f in fl])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eng.run()
+        e1.record()
+        torch.cuda.synchronize()
+        eng.check_status()
+        gpu_s += e0.elapsed_time(e1) * 1e-3
+        out[torch.as_tensor(idx, device="cuda")] = eng.energy[:len(idx)]
+        del eng
+        torch.cuda.empty_cache()
+
+    for k in order:
+        o, v, X = system.fragment_dims(frags[k])
+        nb = o * v * X * 8
+        if chunk and (bytes_ + nb > chunk_bytes or len(frags[chunk[0]]) != len(frags[k])):
+            flush(chunk)
+            chunk, bytes_ = [], 0
+        chunk.append(k)
+        bytes_ += nb
+    flush(chunk)
+    return out, gpu_s
+
+
+@dataclass
+class TrimerSet:
+    trimers: np.ndarray          # [nt, 3]
+    feats: torch.Tensor          # [nt, 9] FP32 device
+    labels: torch.Tensor         # [nt] FP32 log10|dE_IJK|
+    dE: torch.Tensor             # [nt] FP64 dE_IJK
+    trimer_seconds: float        # GPU time spent on the trimer energies
+    lower_seconds: float         # GPU time on monomers and pairs
+
+
+def _index(frags):
+    return {f: k for k, f in enumerate(frags)}
+
+
+def trimer_set(system, r_trimer, rule="two_pairs", precision="bf16", slices_v=8,
+               device_inputs=True, trimers=None) -> TrimerSet:
+    """Candidate trimers (or the given list), their exact-by-the-method corrections, and
+    features built from the dimer corrections of their sub-pairs."""
+    if trimers is None:
+        _, trimers = rimp2.mbe_polymers(system.centroids, 0.0, r_trimer, rule)
+    trimers = np.asarray(trimers, dtype=np.int32).reshape(-1, 3)
+    mons = [(i,) for i in range(system.n)]
+    pairs = sorted({(int(a), int(b)) for t in trimers for a, b in ((t[0], t[1]), (t[0], t[2]), (t[1], t[2]))})
+    tris = [tuple(int(x) for x in t) for t in trimers]
+    low = mons + pairs
+    E_low, s_low = fragment_energies(system, low, precision, slices_v, device_inputs)
+    E_tri, s_tri = fragment_energies(system, tris, precision, slices_v, device_inputs)
+    E = torch.cat([E_low, E_tri])
+    ix = _index(low + tris)
+    dterms = torch.tensor([[ix[p], ix[(p[0],)], ix[(p[1],)]] for p in pairs] or
+                          np.zeros((0, 3)), dtype=torch.int32)
+    dde = rimp2.mbe_corrections(E, dterms, DIMER_SIGNS) if len(pairs) else \
+        torch.zeros(0, dtype=torch.float64, device="cuda")
+    table = torch.zeros((system.n, system.n), dtype=torch.float64, device="cuda")
+    if len(pairs):
+        pa = torch.as_tensor(np.array(pairs), device="cuda", dtype=torch.long)
+        table[pa[:, 0], pa[:, 1]] = dde
+        table[pa[:, 1], pa[:, 0]] = dde
+    tterms = torch.tensor([[ix[t], ix[(t[0], t[1])], ix[(t[0], t[2])], ix[(t[1], t[2])],
+                            ix[(t[0],)], ix[(t[1],)], ix[(t[2],)]] for t in tris] or
+                          np.zeros((0, 7)), dtype=torch.int32)
+    dE, lab = rimp2.mbe_corrections(E, tterms, TRIMER_SIGNS, want_log=True)
+    cen = torch.as_tensor(system.centroids, dtype=torch.float64, device="cuda")
+    nocc = torch.as_tensor(system.nocc, dtype=torch.int32, device="cuda")
+    tri_d = torch.as_tensor(trimers, dtype=torch.int32, device="cuda")
+    feats = rimp2.screen_features(cen, nocc, tri_d, table)
+    return TrimerSet(trimers, feats, lab, dE, s_tri, s_low)
+
+
+class TrimerScreen:
+    """The MLP parameters (FP32 master on the device, BF16 in the forward pass) and its
+    Adam state; feature standardisation constants fixed from the training set."""
+
+    def __init__(self, seed: int = 0):
+        rng = np.random.default_rng(seed)
+        parts = []
+        for (o, i) in ((64, 9), (64, 64), (64, 64), (1, 64)):
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / i), size=o * i))
+            parts.append(np.zeros(o))
+        theta = np.concatenate(parts).astype(np.float32)
+        assert theta.size == rimp2.MLP_PARAMS
+        self.master = torch.as_tensor(theta, device="cuda")
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.t = 0
+        self.mean = torch.zeros(9, dtype=torch.float32, device="cuda")
+        self.std = torch.ones(9, dtype=torch.float32, device="cuda")
+
+    def set_normalization(self, feats: torch.Tensor):
+        f = feats.double().cpu().numpy()
+        self.mean = torch.as_tensor(f.mean(0), dtype=torch.float32, device="cuda")
+        self.std = torch.as_tensor(f.std(0) + 1e-3, dtype=torch.float32, device="cuda")
+
+    def fit(self, feats, labels, epochs=200, batch=512, lr=2e-3, seed=0):
+        n = feats.shape[0]
+        rng = np.random.default_rng(seed)
+        hist = []
+        for ep in range(epochs):
+            perm = torch.as_tensor(rng.permutation(n).astype(np.int32), device="cuda")
+            tot = 0.0
+            for s0 in range(0, n, batch):
+                idx = perm[s0:s0 + batch]
+                g, loss = rimp2.mlp_grad(self.master, feats, labels, idx, idx.numel(),
+                                         self.mean, self.std)
+                self.t += 1
+                rimp2.mlp_adam(self.master, g, self.m, self.v, self.t, lr)
+                tot += float(loss.item()) * idx.numel()
+            hist.append(tot / n)
+        return hist
+
+    def predict(self, feats):
+        return rimp2.mlp_predict(self.master, feats, self.mean, self.std)
+
+    def loss(self, feats, labels):
+        _, l = rimp2.mlp_grad(self.master, feats, labels, None, feats.shape[0], self.mean,
+                              self.std)
+        return float(l.item())
+
+
+def screen_and_judge(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7,
+                     margin_decades=1.0, judge_fraction=0.05, seed=0, judge_precision="fp64"):
+    """Applies the screen to the candidate set `ts` (whose exact corrections are known, so
+    the effect on the MBE3 total is measured directly) and recomputes a random
+    `judge_fraction` of the skipped trimers with the plain method."""
+    pred = screen.predict(ts.feats).cpu().numpy()
+    skip = pred < (np.log10(threshold) - margin_decades)
+    dE = ts.dE.cpu().numpy()
+    nt = len(dE)
+    res = {"candidates": int(nt), "skipped": int(skip.sum()), "kept": int(nt - skip.sum()),
+           "threshold_Eh": threshold, "margin_decades": margin_decades,
+           "skipped_sum_Eh": float(np.sum(dE[skip])),
+           "skipped_abs_sum_Eh": float(np.sum(np.abs(dE[skip]))),
+           "max_skipped_abs_Eh": float(np.max(np.abs(dE[skip]))) if skip.any() else 0.0,
+           "missed_above_threshold": int(np.sum(skip & (np.abs(dE) >= threshold)))}
+    # time saved: the trimer-energy GPU time scales with the trimers computed
+    fl = np.array([_flops(system, t) for t in ts.trimers])
+    res["trimer_flop_fraction_skipped"] = float(fl[skip].sum() / max(fl.sum(), 1.0))
+    res["trimer_seconds_all"] = ts.trimer_seconds
+    res["trimer_seconds_saved_est"] = ts.trimer_seconds * res["trimer_flop_fraction_skipped"]
+    # judge: recompute a held-out random sample of the skipped trimers with the plain method
+    sk = np.nonzero(skip)[0]
+    rng = np.random.default_rng(seed + 12345)
+    nj = int(np.ceil(judge_fraction * len(sk))) if len(sk) else 0
+    if nj:
+        pick = np.sort(rng.choice(sk, nj, replace=False))
+        js = trimer_set(system, None, precision=judge_precision, device_inputs=True,
+                        trimers=ts.trimers[pick]) if judge_precision == "fp64" else None
+        jd = js.dE.cpu().numpy()
+        res["judge_count"] = int(nj)
+        res["judge_max_abs_Eh"] = float(np.max(np.abs(jd)))
+        res["judge_mean_abs_Eh"] = float(np.mean(np.abs(jd)))
+        res["judge_est_skipped_abs_sum_Eh"] = float(np.mean(np.abs(jd)) * len(sk))
+        res["judge_vs_method_max_diff_Eh"] = float(np.max(np.abs(jd - dE[pick])))
+        res["judge_precision"] = judge_precision
+    return res, skip
+
+
+def _flops(system, t):
+    o, v, X = system.fragment_dims(t)
+    return float(o * (o + 1) * v * v * X)
