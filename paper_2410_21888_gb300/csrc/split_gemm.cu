@@ -325,8 +325,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                             ((uint32_t)(SG_BM >> 4) << 24);
+      // kind::f16 instruction descriptor without N: F32 accumulate, BF16 A and B, both
+      // K-major, M = 128; N (a multiple of NT up to 256) is or-ed in per MMA
+      const uint32_t idesc_m = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SG_BM >> 4) << 24);
+      constexpr int kGroup = 256 / NT;
       uint32_t st = 0, ph = 0, te_count = 0;
       int tslot = 0;
       uint32_t tph = 0;
@@ -353,11 +355,15 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             for (int k16 = 0; k16 < 2; ++k16) {
               for (int p = 0; p < slices; ++p) {
                 const uint64_t adesc = sw64_desc(base + p * A_TILE) + (uint64_t)(k16 * 2);
-                for (int q = 0; q + p < slices; ++q) {
+                // one MMA of A_p against the contiguous B tiles q0 .. q0+nq-1: the column
+                // block of B_q lands on the level-(p+q) accumulator at (p+q) * NT
+                for (int q0 = 0; q0 + p < slices; q0 += kGroup) {
+                  const int nq = min(kGroup, slices - p - q0);
                   const uint64_t bdesc =
-                      sw64_desc(base + slices * A_TILE + q * B_TILE) + (uint64_t)(k16 * 2);
+                      sw64_desc(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
                   const uint32_t acc = (kk == c * SG_CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
-                  umma_bf16(tmem_base + (uint32_t)((p + q) * NT), adesc, bdesc, idesc, acc);
+                  umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc,
+                            idesc_m | ((uint32_t)((nq * NT) >> 3) << 17), acc);
                 }
               }
             }
