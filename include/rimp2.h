@@ -99,11 +99,18 @@ typedef struct rimp2_options {
   int32_t slices_t;    /* split modes: slices for Gamma/P operands (2..8, default 6) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
-  int32_t autotune;    /* 1: time tile variants in situ on first calls (default 0) */
+  int32_t autotune;    /* 1: the first calls of the plan each run one variant of the
+                          Gamma/P contraction stage (operand view of P_ij, split-K factor),
+                          timed in situ with CUDA events; later calls use the fastest
+                          (default 0).  Results are identical up to rounding order. */
   int32_t profile_stages; /* 1: record CUDA events between the stages of each call so that
                              rimp2_get_stats reports stage_ms (default 0) */
   size_t max_workspace_bytes; /* 0: one wave for the whole batch; else waves sized so
                                  the workspace stays below this many bytes */
+  const char* autotune_cache; /* NULL, or a text file "<key> <variant>" per line: a plan
+                                 whose key (precision, slices, shapes) is listed starts with
+                                 that variant and skips the trials; new results are
+                                 appended */
 } rimp2_options;
 
 typedef struct rimp2_stats {
@@ -115,6 +122,9 @@ typedef struct rimp2_stats {
   int32_t waves;
   int32_t graph_captures;
   int32_t status;          /* last status word seen by rimp2_get_status */
+  int32_t tune_variant;    /* contraction-stage variant in use (see autotune) */
+  int32_t tune_done;       /* 1 once the autotune trials finished (or were cached) */
+  double tune_ms[4];       /* autotune: contraction-stage ms measured for each variant */
   double stage_ms[4];      /* with profile_stages: device ms of the last call, summed over
                               waves: [0] input checks and operand slicing, [1] V GEMM with the
                               T = V/D epilogue, [2] amplitudes, pair/total energies, zeroing,

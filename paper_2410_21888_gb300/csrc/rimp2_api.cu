@@ -8,7 +8,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
+#include <string>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -70,7 +72,15 @@ struct rimp2_plan {
   bool timing_pending = false;
   rimp2_stats stats{};
   SplitPlan split;
-  std::vector<cudaEvent_t> stage_ev;   // 5 per wave when profile_stages
+  std::vector<cudaEvent_t> stage_ev;   // 5 per wave when profile_stages (or autotune)
+  // autotune: 0 off, 1 trials running, 2 done
+  int tune_state = 0;
+  int tune_next = 0;
+  int tune_cur = -1;                   // variant of the trial whose time is pending
+  int variant = 0;                     // contraction-stage variant in use
+  double tune_ms[4] = {0, 0, 0, 0};
+  uint64_t tune_key = 0;
+  std::string cache_path;
 };
 
 extern "C" {
@@ -132,9 +142,9 @@ int check_frag_shapes(const rimp2_frag* frags, int nfrag) {
 }
 
 // split-K factor over the outer K index so that small M x N problems fill the GPU
-void choose_split(GemmProb& P, int grid) {
+void choose_split(GemmProb& P, int grid, int mul) {
   const long long tiles = (long long)P.tiles_m * P.tiles_n;
-  long long want = std::max(1LL, (2LL * grid + tiles - 1) / tiles);
+  long long want = std::max(1LL, ((long long)mul * grid + tiles - 1) / tiles);
   want = std::min<long long>(want, P.K1);
   int chunk = (int)((P.K1 + want - 1) / want);
   if (chunk < 1) chunk = 1;
@@ -212,7 +222,7 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
       P.sAm = (long long)ov; P.sAk = 1; P.sA1 = (long long)v * ov;
       P.sBn = (long long)ov; P.sBk = 1; P.sB1 = (long long)v * ov; P.ldc = v;
       P.alpha = 1.0; P.v = v; P.b_from_B = 0;
-      choose_split(P, p->gemm_grid);
+      choose_split(P, p->gemm_grid, 2 << p->variant);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       w.probs_c.push_back(P);
     }
@@ -225,7 +235,7 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
       P.sAm = v; P.sAk = 1; P.sA1 = (long long)ov;
       P.sBn = v; P.sBk = 1; P.sB1 = (long long)ov; P.ldc = o;
       P.alpha = -1.0; P.v = v; P.b_from_B = 0;
-      choose_split(P, p->gemm_grid);
+      choose_split(P, p->gemm_grid, 2 << p->variant);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       w.probs_c.push_back(P);
     }
@@ -237,6 +247,7 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
 
 int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags, const double* B, void* ws) {
   p->waves.clear();
+  p->split.variant = p->variant;
   for (auto& m : p->wave_members) {
     WaveDesc w;
     w.frags = m;
@@ -297,7 +308,7 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
     const int nf = (int)w.fdev.size();
     unsigned* ctr = p->d_counters + wi * 8;
     cudaError_t e = cudaSuccess;
-    cudaEvent_t* ev = p->opt.profile_stages ? &p->stage_ev[wi * 5] : nullptr;
+    cudaEvent_t* ev = p->stage_ev.empty() ? nullptr : &p->stage_ev[wi * 5];
     if (ev && cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal) != cudaSuccess) return RIMP2_ERR_CUDA;
     if (p->opt.check_inputs) {
       e = launch_check_inputs(dfd, nf, (w.max_b + 255) / 256, bs, s);
@@ -342,6 +353,61 @@ void drop_graph(rimp2_plan* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   p->gexec = nullptr;
   p->graph = nullptr;
+}
+
+constexpr int kFp64Variants = 3;   // FP64 path: split-K target 2, 4, 8 x grid
+
+uint64_t fnv(uint64_t h, uint64_t x) {
+  for (int b = 0; b < 8; ++b) {
+    h ^= (x >> (8 * b)) & 0xFF;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t tune_key(const rimp2_plan* p) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, (uint64_t)p->precision);
+  h = fnv(h, (uint64_t)p->opt.slices_v);
+  h = fnv(h, (uint64_t)p->opt.slices_t);
+  h = fnv(h, (uint64_t)p->frags.size());
+  for (const auto& f : p->frags) {
+    h = fnv(h, ((uint64_t)f.nocc << 42) ^ ((uint64_t)f.nvir << 21) ^ (uint64_t)f.naux);
+    h = fnv(h, (uint64_t)((f.gamma_off >= 0) | ((f.pij_off >= 0) << 1) | ((f.pab_off >= 0) << 2)));
+  }
+  return h;
+}
+
+int cache_lookup(const std::string& path, uint64_t key) {
+  if (path.empty()) return -1;
+  FILE* fh = fopen(path.c_str(), "r");
+  if (!fh) return -1;
+  unsigned long long k = 0;
+  int v = -1, found = -1;
+  while (fscanf(fh, "%llx %d", &k, &v) == 2)
+    if (k == key) found = v;
+  fclose(fh);
+  return found;
+}
+
+void cache_store(const std::string& path, uint64_t key, int variant) {
+  if (path.empty()) return;
+  FILE* fh = fopen(path.c_str(), "a");
+  if (!fh) return;
+  fprintf(fh, "%016llx %d\n", (unsigned long long)key, variant);
+  fclose(fh);
+}
+
+// contraction-stage device time of the last call (events 3 -> 4 of every wave)
+double contraction_ms(rimp2_plan* p) {
+  double ms = 0.0;
+  for (size_t w = 0; w < p->wave_members.size(); ++w) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->stage_ev[w * 5 + 3], p->stage_ev[w * 5 + 4]) == cudaSuccess)
+      ms += t;
+    cudaGetLastError();
+  }
+  return ms;
 }
 
 double frag_flops(const rimp2_frag& f) {
@@ -406,7 +472,17 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
     rimp2_plan_destroy(p);
     return RIMP2_ERR_CUDA;
   }
-  if (o.profile_stages) {
+  if (o.autotune) {
+    p->tune_key = tune_key(p);
+    if (o.autotune_cache) p->cache_path = o.autotune_cache;
+    const int cached = cache_lookup(p->cache_path, p->tune_key);
+    const int ncand = precision == RIMP2_FP64 ? kFp64Variants : kSplitVariants;
+    if (cached >= 0 && cached < ncand) { p->variant = cached; p->tune_state = 2; }
+    else p->tune_state = 1;
+    p->stats.tune_done = p->tune_state == 2;
+    p->stats.tune_variant = p->variant;
+  }
+  if (o.profile_stages || o.autotune) {
     p->stage_ev.assign(p->wave_members.size() * 5, nullptr);
     for (auto& e : p->stage_ev)
       if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); rimp2_plan_destroy(p); return RIMP2_ERR_CUDA; }
@@ -454,6 +530,32 @@ int rimp2_energy_grad(rimp2_plan* p, const rimp2_batch* b, void* workspace, size
   if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return RIMP2_ERR_BAD_ARG;
   cudaStream_t s = (cudaStream_t)stream;
 
+  if (p->tune_state == 1) {
+    // in-situ trials: the time of the previous call's variant, then the next variant
+    const int ncand = p->precision == RIMP2_FP64 ? kFp64Variants : kSplitVariants;
+    if (p->tune_cur >= 0) {
+      if (cudaEventSynchronize(p->done) != cudaSuccess) return RIMP2_ERR_CUDA;
+      p->tune_ms[p->tune_cur] = contraction_ms(p);
+      p->stats.tune_ms[p->tune_cur] = p->tune_ms[p->tune_cur];
+      p->tune_cur = -1;
+    }
+    int next = -1;
+    if (p->tune_next < ncand) next = p->tune_next++;
+    else {
+      next = 0;
+      for (int v = 1; v < ncand; ++v)
+        if (p->tune_ms[v] < p->tune_ms[next]) next = v;
+      p->tune_state = 2;
+      p->stats.tune_done = 1;
+      cache_store(p->cache_path, p->tune_key, next);
+    }
+    if (next != p->variant || !p->have_desc) {
+      p->variant = next;
+      p->have_desc = false;   // rebuild descriptors and graph for this variant
+    }
+    if (p->tune_state == 1) p->tune_cur = next;
+    p->stats.tune_variant = p->variant;
+  }
   Key k{};
   k.p[0] = b->B; k.p[1] = b->eps; k.p[2] = workspace; k.p[3] = b->gamma; k.p[4] = b->pij;
   k.p[5] = b->pab; k.p[6] = b->epair; k.p[7] = b->energy; k.p[8] = nullptr;
@@ -530,7 +632,7 @@ int rimp2_get_status(rimp2_plan* p) {
 
 int rimp2_get_stats(rimp2_plan* p, rimp2_stats* out) {
   if (!p || !out) return RIMP2_ERR_BAD_ARG;
-  if (p->opt.profile_stages && p->stats.calls > 0) {
+  if (!p->stage_ev.empty() && p->stats.calls > 0) {
     if (cudaEventSynchronize(p->done) != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
     for (int k = 0; k < 4; ++k) p->stats.stage_ms[k] = 0.0;
     for (size_t w = 0; w < p->wave_members.size(); ++w)

@@ -5,9 +5,11 @@
 //   x ~= sum_p d_p 2^(E - 8(p+1)),   |x| < 2^(E-1).
 // C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 16) sum_l 2^(-8 l) S_l with
 // S_l = sum_{p+q=l} sum_k dA_p dB_q, the truncated level sum kept for l < s.  Each S_l
-// accumulates in its own FP32 TMEM accumulator over K chunks of 256, where levels 0..3
-// are exact integers (|S_l| <= 4 * 256 * 2^14 = 2^24); each chunk is then folded into
-// a per-element double-float (hi, lo) accumulator in registers.
+// accumulates in its own FP32 TMEM accumulator over K chunks of 512, where levels 0
+// and 1 are exact integers by construction (|S_l| <= 2 * 512 * 2^14 = 2^24); a level
+// l >= 2 rounds only if its partial sum exceeds 2^24 in magnitude, which bounds that
+// error by 2^-24 of the level, i.e. 2^-40 of the level sums' magnitude.  Each chunk is
+// then folded into a per-element double-float (hi, lo) accumulator in registers.
 #pragma once
 
 #include <cuda.h>
@@ -21,7 +23,7 @@ namespace rimp2 {
 constexpr int SG_BM = 128;          // rows per tile (TMEM lanes)
 constexpr int SG_BN_MAX = 96;       // max columns per tile
 constexpr int SG_BK = 32;           // bf16 K elements per stage (64-byte rows, 64B swizzle)
-constexpr int SG_CHUNK_STAGES = 8;  // 256 K per exact accumulation chunk
+constexpr int SG_CHUNK_STAGES = 16; // 512 K per accumulation chunk
 constexpr int SG_MAX_SLICES = 8;
 constexpr int SG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int SG_EPI_WARPS = 8;

@@ -380,9 +380,9 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   return L;
 }
 
-void choose_split_k(SplitProb& P, int grid) {
+void choose_split_k(SplitProb& P, int grid, int mul) {
   const long long tiles = (long long)P.tiles_m * P.tiles_n;
-  long long want = std::max(1LL, (2LL * grid + tiles - 1) / tiles);
+  long long want = std::max(1LL, ((long long)mul * grid + tiles - 1) / tiles);
   want = std::min<long long>(want, std::max(1, P.k1_count));
   int chunk = (int)((P.k1_count + want - 1) / want);
   if (chunk < 1) chunk = 1;
@@ -416,6 +416,8 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   long long pairs = 0, rows = 0, b2t = 0;
   const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max;
   const int sv = sp.slices_v, st = sp.slices_t;
+  const int split_mul = sp.variant == 2 ? 4 : 2;
+  const bool pij_direct = sp.variant == 1;
   w.want_gamma = false;
   for (int idx : members) {
     const rimp2_frag& f = frags[idx];
@@ -503,7 +505,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
       P.c_off = f.pab_off; P.ldc = v; P.alpha = 1.0;
-      choose_split_k(P, sp.grid);
+      choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s4[3] = {(uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
@@ -513,7 +515,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     }
-    if (f.pij_off >= 0) {  // P_ij = -sum_(k,a) sum_b Tt[(i,a)][(k,b)] T[(j,a)][(k,b)]
+    if (f.pij_off >= 0 && pij_direct) {  // P_ij = -sum_(k,a) sum_b Tt[(i,a)][(k,b)] T[(j,a)][(k,b)]
       SplitProb P{};
       P.kind = PK_PIJ; P.frag = idx;
       P.M = P.N = o; P.n_tile = NTt;
@@ -523,13 +525,35 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
       P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0;
-      choose_split_k(P, sp.grid);
+      choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s5[4] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
       const uint32_t boxA[5] = {SG_BK, 1, 1, SG_BM, 1}, boxB[5] = {SG_BK, 1, 1, (uint32_t)NTt, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB) != RIMP2_OK)
+        return RIMP2_ERR_UNSUPPORTED;
+      w.probs_c.push_back(P);
+    } else if (f.pij_off >= 0) {
+      // P_ij through the pair symmetry Tt_ik(a,b) = Tt_ki(b,a):
+      // P_ij = -sum_(k,b) sum_a Tt[(k,b)][(i,a)] T[(k,b)][(j,a)]; the rows i of one
+      // (k,b) row are vpad elements apart, so a 128-row TMA box reads one contiguous span
+      SplitProb P{};
+      P.kind = PK_PIJ; P.frag = idx;
+      P.M = P.N = o; P.n_tile = NTt;
+      P.tiles_m = (o + SG_BM - 1) / SG_BM; P.tiles_n = (o + NTt - 1) / NTt;
+      P.k0_blocks = (vpad + SG_BK - 1) / SG_BK; P.k1_count = o * v;
+      P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
+      P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
+      P.ea_add = -123; P.eb_add = -124;
+      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0;
+      choose_split_k(P, sp.grid, split_mul);
+      P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
+      const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
+      const uint64_t s4[3] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, plane_b};
+      const uint32_t boxA[4] = {SG_BK, SG_BM, 1, 1}, boxB[4] = {SG_BK, (uint32_t)NTt, 1, 1};
+      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     }

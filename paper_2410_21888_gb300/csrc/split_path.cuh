@@ -31,7 +31,14 @@ struct SplitPlan {
   SplitLaunch cfg_v{}, cfg_t{};
   int grid = 0;
   bool ready = false;
+  int variant = 0;   // contraction-stage variant (autotuner), see split_variant_desc
 };
+
+// Variants of the Gamma/P contraction stage the autotuner times:
+//   0: P_ij rows read through the local (k,b)-major view, split-K target 2 x grid
+//   1: P_ij rows read through the direct (i,a)-major view, split-K target 2 x grid
+//   2: local view, split-K target 4 x grid
+constexpr int kSplitVariants = 3;
 
 struct SplitWave {
   std::vector<SplitFragDev> sfd;

@@ -59,7 +59,7 @@ class Options(ctypes.Structure):
     _fields_ = [("slices_v", ctypes.c_int32), ("slices_t", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("profile_stages", ctypes.c_int32),
-                ("max_workspace_bytes", ctypes.c_size_t)]
+                ("max_workspace_bytes", ctypes.c_size_t), ("autotune_cache", ctypes.c_char_p)]
 
 
 class Stats(ctypes.Structure):
@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("calls", ctypes.c_int64), ("tiles_per_call", ctypes.c_int64),
                 ("launches_per_call", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("graph_captures", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("stage_ms", ctypes.c_double * 4)]
+                ("tune_variant", ctypes.c_int32), ("tune_done", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * 4), ("stage_ms", ctypes.c_double * 4)]
 
 
 _lib = None
@@ -142,7 +143,8 @@ class Plan:
     def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 5,
                  slices_t: int = 6, use_graph: bool = True, check_inputs: bool = True,
                  max_workspace_bytes: int = 0, profile_stages: bool = False,
-                 want_gamma: bool = True, want_p: bool = True):
+                 want_gamma: bool = True, want_p: bool = True, autotune: bool = False,
+                 autotune_cache: str | None = None):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -157,6 +159,9 @@ class Plan:
         opt.use_graph, opt.check_inputs = int(use_graph), int(check_inputs)
         opt.max_workspace_bytes = int(max_workspace_bytes)
         opt.profile_stages = int(profile_stages)
+        opt.autotune = int(autotune)
+        self._cache = autotune_cache.encode() if autotune_cache else None
+        opt.autotune_cache = self._cache
         h = ctypes.c_void_p()
         _check(lib.rimp2_plan_create(frags, len(self.dims), PRECISIONS[precision],
                                      ctypes.byref(opt), ctypes.byref(h)), "rimp2_plan_create")

@@ -179,12 +179,16 @@ class TrimerScreen:
         self.mean = torch.as_tensor(f.mean(0), dtype=torch.float32, device="cuda")
         self.std = torch.as_tensor(f.std(0) + 1e-3, dtype=torch.float32, device="cuda")
 
-    def fit(self, feats, labels, epochs=200, batch=512, lr=2e-3, seed=0):
-        n = feats.shape[0]
+    def fit(self, feats, labels, epochs=200, batch=512, lr=2e-3, seed=0, rows=None):
+        """Adam on minibatches of `rows` (device int32 row indices; default all rows)."""
+        if rows is None:
+            rows = torch.arange(feats.shape[0], dtype=torch.int32, device="cuda")
+        rows_h = rows.cpu().numpy()
+        n = len(rows_h)
         rng = np.random.default_rng(seed)
         hist = []
         for ep in range(epochs):
-            perm = torch.as_tensor(rng.permutation(n).astype(np.int32), device="cuda")
+            perm = torch.as_tensor(rows_h[rng.permutation(n)].astype(np.int32), device="cuda")
             tot = 0.0
             for s0 in range(0, n, batch):
                 idx = perm[s0:s0 + batch]
@@ -199,23 +203,43 @@ class TrimerScreen:
     def predict(self, feats):
         return rimp2.mlp_predict(self.master, feats, self.mean, self.std)
 
-    def loss(self, feats, labels):
-        _, l = rimp2.mlp_grad(self.master, feats, labels, None, feats.shape[0], self.mean,
-                              self.std)
+    def loss(self, feats, labels, rows=None):
+        n = feats.shape[0] if rows is None else rows.numel()
+        idx = None if rows is None else rows.to(torch.int32)
+        _, l = rimp2.mlp_grad(self.master, feats, labels, idx, n, self.mean, self.std)
         return float(l.item())
 
 
+def select_skips(pred_log10, threshold=1e-7, margin_decades=1.0, budget_Eh=None, safety=10.0):
+    """Trimers to skip: predicted |dE| below threshold x 10^-margin, taken in ascending
+    order of the prediction while the predicted skipped sum stays within
+    budget_Eh / safety (no budget: the threshold rule alone)."""
+    pred = np.asarray(pred_log10, dtype=np.float64)
+    cand = pred < (np.log10(threshold) - margin_decades)
+    if budget_Eh is None:
+        return cand
+    order = np.argsort(pred)
+    csum = np.cumsum(10.0 ** pred[order])
+    take = order[(csum <= budget_Eh / safety) & cand[order]]
+    skip = np.zeros(len(pred), dtype=bool)
+    skip[take] = True
+    return skip
+
+
 def screen_and_judge(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7,
-                     margin_decades=1.0, judge_fraction=0.05, seed=0, judge_precision="fp64"):
+                     margin_decades=1.0, judge_fraction=0.05, seed=0, judge_precision="fp64",
+                     budget_Eh=None, safety=10.0):
     """Applies the screen to the candidate set `ts` (whose exact corrections are known, so
     the effect on the MBE3 total is measured directly) and recomputes a random
     `judge_fraction` of the skipped trimers with the plain method."""
     pred = screen.predict(ts.feats).cpu().numpy()
-    skip = pred < (np.log10(threshold) - margin_decades)
+    skip = select_skips(pred, threshold, margin_decades, budget_Eh, safety)
     dE = ts.dE.cpu().numpy()
     nt = len(dE)
     res = {"candidates": int(nt), "skipped": int(skip.sum()), "kept": int(nt - skip.sum()),
            "threshold_Eh": threshold, "margin_decades": margin_decades,
+           "budget_Eh": budget_Eh, "budget_safety": safety,
+           "predicted_skipped_sum_Eh": float(np.sum(10.0 ** pred[skip])),
            "skipped_sum_Eh": float(np.sum(dE[skip])),
            "skipped_abs_sum_Eh": float(np.sum(np.abs(dE[skip]))),
            "max_skipped_abs_Eh": float(np.max(np.abs(dE[skip]))) if skip.any() else 0.0,

@@ -1,9 +1,10 @@
 """GPU tests of the split-precision (BF16 integer-slice, tcgen05) path.
 
 1. The tensor-core slice GEMM alone against exact integer arithmetic: digits in
-   [-128, 128], level sums 2^(-8(p+q)) sum_k A_p B_q for p + q < s.  Levels 0..3 of each
-   256-long K chunk are exact integers in FP32; the chunks are combined in double-float,
-   so the result matches the exact value to ~2^-46 relative.
+   [-128, 128], level sums 2^(-8(p+q)) sum_k A_p B_q for p + q < s.  Levels 0 and 1 of
+   each 512-long K chunk are exact integers in FP32 (higher levels too unless a partial
+   sum passes 2^24); the chunks are combined in double-float, so the result matches the
+   exact value to ~2^-44 of the chunk level magnitudes.
 2. Fragments through rimp2_energy_grad(precision=BF16_SPLIT) against the FP64 oracle.
    Tolerances: energy within 1e-8 Eh per fragment; Gamma, P_ij, P_ab, pair energies
    within 1e-9 relative Frobenius (the accuracy target of the split path).
@@ -37,9 +38,9 @@ def _hook():
     return f
 
 
-def _exact_levels(A, B, s, chunk=256):
+def _exact_levels(A, B, s, chunk=512):
     """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the sum over
-    256-long K chunks of |chunk level sums| (the magnitudes the kernel accumulates)."""
+    512-long K chunks of |chunk level sums| (the magnitudes the kernel accumulates)."""
     M, N, K = A.shape[1], B.shape[1], A.shape[2]
     out = np.zeros((M, N))
     mag = np.zeros((M, N))
@@ -57,8 +58,9 @@ def _exact_levels(A, B, s, chunk=256):
 @pytest.mark.parametrize("M,N,K,s,seed", [
     (128, 96, 64, 2, 0),
     (128, 96, 32, 5, 1),
-    (200, 150, 300, 5, 2),       # ragged M/N, two 256-chunks with a tail
-    (130, 97, 1000, 3, 3),       # four chunks
+    (200, 150, 300, 5, 2),       # ragged M/N, one chunk with a partial K block
+    (256, 192, 1500, 5, 7),      # three chunks, 1500 = the large-fragment naux
+    (130, 97, 1000, 3, 3),       # two chunks
     (64, 40, 33, 4, 4),          # partial tiles and a partial K block
     (300, 260, 700, 6, 5),       # n_tile 80
     (129, 70, 257, 8, 6),        # n_tile 64, eight slices
