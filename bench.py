@@ -171,6 +171,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage-k", type=int, default=0, choices=[0, 16, 32],
+                    help="K per tensor-core pipeline stage (0: library default)")
+    ap.add_argument("--n-tile", type=int, default=0, choices=[0, 64, 80, 96])
+    ap.add_argument("--slices-t", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the plain FP64 path reported beside the split path")
     args = ap.parse_args()
@@ -201,7 +205,9 @@ def main():
     results = {}
     for prec in precs:
         try:
-            eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True)
+            eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True,
+                               stage_k=args.stage_k, n_tile=args.n_tile,
+                               slices_t=args.slices_t)
         except rimp2.Rimp2Error as e:
             if e.code == -8:
                 continue
@@ -281,7 +287,7 @@ def main():
                 "kernel": "k_gemm_f64 (" + ("Gamma/P_ab/P_ij" if k == 3 else "V") + ")",
                 "peak_source": "measured DFMA peak (probes/dfma_peak.cu)"}
     else:
-        sv, stt = 5, 6
+        sv, stt = 5, args.slices_t
         prod_v, prod_t = sv * (sv + 1) // 2, stt * (stt + 1) // 2
         k = 3 if sm[3] >= sm[1] else 1
         Fk = F_c * prod_t if k == 3 else F_v * prod_v

@@ -24,6 +24,12 @@ extern "C" {
 int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t kpad, int32_t slices,
                              const void* A, const void* B, double* C, void* stream);
 
+/* Same with an explicit pipeline stage depth in K: stage_k = 16 (32-byte swizzled rows)
+ * or 32 (64-byte swizzled rows). */
+int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32_t kpad, int32_t slices,
+                               int32_t stage_k, const void* A, const void* B, double* C,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -431,7 +431,9 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   rimp2_default_options(&o);
   if (opt) o = *opt;
   if (precision != RIMP2_FP64 &&
-      (o.slices_v < 2 || o.slices_v > 8 || o.slices_t < 2 || o.slices_t > 8))
+      (o.slices_v < 2 || o.slices_v > 8 || o.slices_t < 2 || o.slices_t > 8 ||
+       (o.stage_k != 0 && o.stage_k != 16 && o.stage_k != 32) ||
+       (o.n_tile != 0 && o.n_tile != 64 && o.n_tile != 80 && o.n_tile != 96)))
     return RIMP2_ERR_UNSUPPORTED;
   rimp2_plan* p = new (std::nothrow) rimp2_plan();
   if (!p) return RIMP2_ERR_NOMEM;

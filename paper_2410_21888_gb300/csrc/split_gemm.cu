@@ -9,6 +9,8 @@
 // loads in flight, frees its TMEM and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "split_gemm.cuh"
 
 namespace rimp2 {
@@ -137,11 +139,16 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// UMMA shared-memory descriptor, K-major operand with 64-byte swizzle: rows of 64 bytes,
-// 8-row core groups 512 bytes apart (SBO), descriptor version 1, layout SWIZZLE_64B (4).
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(512u >> 4) << 32) |
-         ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
+// UMMA shared-memory descriptor of a K-major operand whose rows hold BK bf16 (2 BK
+// bytes) with the matching swizzle: 8-row core groups 16 BK bytes apart (SBO),
+// descriptor version 1, layout SWIZZLE_64B (4) for 64-byte rows, SWIZZLE_32B (6) for
+// 32-byte rows.
+template <int BK>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  constexpr uint64_t layout = BK == 32 ? 4u : 6u;
+  constexpr uint64_t sbo = (8u * 2u * BK) >> 4;
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | (sbo << 32) |
+         ((uint64_t)1u << 46) | (layout << 61);
 }
 
 // ------------------------------------------------------------------ double-float
@@ -225,13 +232,14 @@ __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm,
 
 // ------------------------------------------------------------------ the kernel
 
-template <int NT>
+template <int NT, int BK>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, Bases bs,
              unsigned* __restrict__ counter, int slices, int stages) {
   constexpr int NC = NT / 2;                 // columns per epilogue thread
-  constexpr uint32_t A_TILE = SG_BM * 64;    // bytes of one 128 x 32 bf16 tile
-  constexpr uint32_t B_TILE = NT * 64;
+  constexpr uint32_t A_TILE = SG_BM * BK * 2;   // bytes of one 128 x BK bf16 tile
+  constexpr uint32_t B_TILE = NT * BK * 2;
+  constexpr int CHUNK_STAGES = SG_CHUNK_K / BK;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -301,7 +309,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           pending[st] = true;
           pend_ph[st] = ph;
           const int k1 = ti.k1b + kk / P->k0_blocks;
-          const int x = (kk % P->k0_blocks) * SG_BK;
+          const int x = (kk % P->k0_blocks) * BK;
           const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
           for (int p = 0; p < slices; ++p)
             tma_operand(base + p * A_TILE, &P->tmA, full + st, P->a_mode, x, rowA, k1, P->div5, p);
@@ -340,28 +348,28 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
         if (tslot == 0) tph ^= 1u;
         if (t >= total) break;
         const TileInfo ti = decode_tile(probs, nprobs, t, NT);
-        const int chunks = (ti.nK + SG_CHUNK_STAGES - 1) / SG_CHUNK_STAGES;
+        const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
         bool ok = true;
         for (int c = 0; c < chunks && ok; ++c) {
           if (!mbar_wait(tmem_empty, (te_count & 1u) ^ 1u, abort_flag)) { ok = false; break; }
           ++te_count;
           tc_fence_after();
-          const int kend = min(ti.nK, (c + 1) * SG_CHUNK_STAGES);
-          for (int kk = c * SG_CHUNK_STAGES; kk < kend; ++kk) {
+          const int kend = min(ti.nK, (c + 1) * CHUNK_STAGES);
+          for (int kk = c * CHUNK_STAGES; kk < kend; ++kk) {
             if (!mbar_wait(full + st, ph, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
 #pragma unroll
-            for (int k16 = 0; k16 < 2; ++k16) {
+            for (int k16 = 0; k16 < BK / 16; ++k16) {
               for (int p = 0; p < slices; ++p) {
-                const uint64_t adesc = sw64_desc(base + p * A_TILE) + (uint64_t)(k16 * 2);
+                const uint64_t adesc = smem_desc<BK>(base + p * A_TILE) + (uint64_t)(k16 * 2);
                 // one MMA of A_p against the contiguous B tiles q0 .. q0+nq-1: the column
                 // block of B_q lands on the level-(p+q) accumulator at (p+q) * NT
                 for (int q0 = 0; q0 + p < slices; q0 += kGroup) {
                   const int nq = min(kGroup, slices - p - q0);
                   const uint64_t bdesc =
-                      sw64_desc(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
-                  const uint32_t acc = (kk == c * SG_CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
+                      smem_desc<BK>(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
+                  const uint32_t acc = (kk == c * CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
                   umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc,
                             idesc_m | ((uint32_t)((nq * NT) >> 3) << 17), acc);
                 }
@@ -396,7 +404,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       if (t >= total) break;
       const TileInfo ti = decode_tile(probs, nprobs, t, NT);
       if (ti.skip) continue;
-      const int chunks = (ti.nK + SG_CHUNK_STAGES - 1) / SG_CHUNK_STAGES;
+      const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
       float acc_h[NC], acc_l[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) { acc_h[c] = 0.f; acc_l[c] = 0.f; }
@@ -405,19 +413,33 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
         if (!mbar_wait(tmem_full, tf_count & 1u, abort_flag)) { ok = false; break; }
         ++tf_count;
         tc_fence_after();
-        for (int l = 0; l < slices; ++l) {
+        // Levels 0..2 are folded into (hi, lo) by error-free sums; levels >= 3 carry at
+        // most 2^-24 of the value and are accumulated into lo directly (FMA).
+        for (int l = slices - 1; l >= 0; --l) {
           float v[NC];
 #pragma unroll
           for (int g = 0; g < NC / 8; ++g)
             tmem_ld8(lane_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
           tmem_wait_ld();
           const float sc = __int_as_float((127 - 8 * l) << 23);   // 2^(-8 l)
+          if (l >= 3) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            const df s = two_sum(acc_h[c], v[c] * sc);
-            acc_h[c] = s.h;
-            acc_l[c] += s.l;
+            for (int c = 0; c < NC; ++c) acc_l[c] = fmaf(v[c], sc, acc_l[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const df s2 = two_sum(acc_h[c], v[c] * sc);
+              acc_h[c] = s2.h;
+              acc_l[c] += s2.l;
+            }
           }
+        }
+        // renormalise so that lo stays within half an ulp of hi across chunks
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const df r = two_sum(acc_h[c], acc_l[c]);
+          acc_h[c] = r.h;
+          acc_l[c] = r.l;
         }
         tc_fence_before();
         __syncwarp();
@@ -492,36 +514,41 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
 
 // ------------------------------------------------------------------ host side
 
-SplitLaunch split_launch_config(int slices) {
+SplitLaunch split_launch_config(int slices, int bk, int n_tile) {
   SplitLaunch c{};
   c.slices = slices;
-  c.n_tile_max = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
-  const size_t stage = (size_t)slices * (SG_BM * 64 + c.n_tile_max * 64);
+  c.bk = bk == 16 ? 16 : 32;
+  const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
+  c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : widest;
+  const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * c.bk * 2;
   const size_t budget = 227 * 1024 - 1024 - 256;
   int st = (int)(budget / stage);
-  if (st > 4) st = 4;
+  if (st > 8) st = 8;
   if (st < 1) st = 1;
   c.stages = st;
   c.smem = 1024 + (size_t)st * stage + 256;
   return c;
 }
 
-template <int NT>
+template <int NT, int BK>
 static cudaError_t launch_nt(const SplitProb* d_probs, int nprobs, long long total, Bases bs,
                              unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
-  k_split_gemm<NT><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs, counter,
-                                                     cfg.slices, cfg.stages);
+  k_split_gemm<NT, BK><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs, counter,
+                                                         cfg.slices, cfg.stages);
   return cudaGetLastError();
 }
 
 // Opt in to the large dynamic shared memory once per device, outside any capture.
 cudaError_t split_gemm_prepare() {
   const int bytes = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_split_gemm<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_split_gemm<80>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaSuccess;
+#define RIMP2_PREP(NT, BK)                                                                  \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_split_gemm<NT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             bytes);
+  RIMP2_PREP(96, 32) RIMP2_PREP(80, 32) RIMP2_PREP(64, 32)
+  RIMP2_PREP(96, 16) RIMP2_PREP(80, 16) RIMP2_PREP(64, 16)
+#undef RIMP2_PREP
   return e;
 }
 
@@ -529,10 +556,17 @@ cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long to
                               unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   const long long g = total_tiles < grid ? total_tiles : grid;
+  if (cfg.bk == 32) {
+    switch (cfg.n_tile_max) {
+      case 96: return launch_nt<96, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+      case 80: return launch_nt<80, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+      default: return launch_nt<64, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    }
+  }
   switch (cfg.n_tile_max) {
-    case 96: return launch_nt<96>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-    case 80: return launch_nt<80>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-    default: return launch_nt<64>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    case 96: return launch_nt<96, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    case 80: return launch_nt<80, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    default: return launch_nt<64, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
   }
 }
 
@@ -563,8 +597,10 @@ int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dim
     es[i] = 1;
     if (i > 0) s[i - 1] = strides_bytes[i - 1];
   }
+  if (box[0] != 16 && box[0] != 32) return RIMP2_ERR_UNSUPPORTED;
+  const CUtensorMapSwizzle sw = box[0] == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
-                        d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? RIMP2_OK : RIMP2_ERR_UNSUPPORTED;
 }

@@ -22,8 +22,9 @@ namespace rimp2 {
 
 constexpr int SG_BM = 128;          // rows per tile (TMEM lanes)
 constexpr int SG_BN_MAX = 96;       // max columns per tile
-constexpr int SG_BK = 32;           // bf16 K elements per stage (64-byte rows, 64B swizzle)
-constexpr int SG_CHUNK_STAGES = 16; // 512 K per accumulation chunk
+constexpr int SG_CHUNK_K = 512;     // K elements per accumulation chunk
+// K per pipeline stage: 32 (64-byte rows, 64B swizzle) or 16 (32-byte rows, 32B swizzle);
+// the smaller stage fits twice as many stages in shared memory
 constexpr int SG_MAX_SLICES = 8;
 constexpr int SG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int SG_EPI_WARPS = 8;
@@ -64,12 +65,15 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
 
 struct SplitLaunch {
   int slices;     // s (levels); same for every problem of one launch
+  int bk;         // K elements per pipeline stage (16 or 32)
   int n_tile_max; // widest n_tile of the launch (smem layout)
   int stages;     // pipeline depth
   size_t smem;    // dynamic shared memory bytes
 };
 
-SplitLaunch split_launch_config(int slices);
+// n_tile: columns per level accumulator (0: widest that fits 512 TMEM columns; else 64,
+// 80 or 96, capped by the TMEM budget)
+SplitLaunch split_launch_config(int slices, int bk = 32, int n_tile = 0);
 cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles,
                               Bases bs, unsigned* counter, const SplitLaunch& cfg, int grid,
                               cudaStream_t s);
@@ -77,6 +81,7 @@ int split_gemm_grid();
 cudaError_t split_gemm_prepare();
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+// box[0] must equal bk (16 -> 32B swizzle, 32 -> 64B swizzle)
 int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
                 const uint64_t* strides_bytes, const uint32_t* box);
 

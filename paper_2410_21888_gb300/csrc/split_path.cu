@@ -341,8 +341,8 @@ int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.precision = precision;
   sp.slices_v = opt.slices_v;
   sp.slices_t = opt.slices_t;
-  sp.cfg_v = split_launch_config(sp.slices_v);
-  sp.cfg_t = split_launch_config(sp.slices_t);
+  sp.cfg_v = split_launch_config(sp.slices_v, opt.stage_k ? opt.stage_k : 32, opt.n_tile);
+  sp.cfg_t = split_launch_config(sp.slices_t, opt.stage_k ? opt.stage_k : 32, opt.n_tile);
   sp.grid = split_gemm_grid();
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   sp.ready = true;
@@ -415,6 +415,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   size_t off = 0;
   long long pairs = 0, rows = 0, b2t = 0;
   const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max;
+  const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk;
   const int sv = sp.slices_v, st = sp.slices_t;
   const int split_mul = sp.variant == 2 ? 4 : 2;
   const bool pij_direct = sp.variant == 1;
@@ -459,7 +460,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.kind = PK_V; P.frag = idx;
       P.M = P.N = ov; P.n_tile = NTv;
       P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (ov + NTv - 1) / NTv;
-      P.ksplit = 1; P.k0_blocks = (X + SG_BK - 1) / SG_BK; P.k1_count = 1; P.k1_chunk = 1;
+      P.ksplit = 1; P.k0_blocks = (X + BKv - 1) / BKv; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
       P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ov; P.alpha = 1.0;
@@ -467,7 +468,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
       const uint64_t str[2] = {(uint64_t)xpad * 2, (uint64_t)ov * xpad * 2};
-      const uint32_t boxA[3] = {SG_BK, SG_BM, 1}, boxB[3] = {SG_BK, (uint32_t)NTv, 1};
+      const uint32_t boxA[3] = {BKv, SG_BM, 1}, boxB[3] = {BKv, (uint32_t)NTv, 1};
       if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -479,7 +480,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.kind = PK_GAMMA; P.frag = idx;
       P.M = ov; P.N = X; P.n_tile = NTt;
       P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTt - 1) / NTt;
-      P.ksplit = 1; P.k0_blocks = (RL + SG_BK - 1) / SG_BK; P.k1_count = 1; P.k1_chunk = 1;
+      P.ksplit = 1; P.k0_blocks = (RL + BKt - 1) / BKt; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
       P.eb_off = s.scal; P.eb_add = 0;
@@ -489,7 +490,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       const uint64_t sA[2] = {(uint64_t)RL * 2, plane_b};
       const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
       const uint64_t sB[2] = {(uint64_t)RL * 2, (uint64_t)X * RL * 2};
-      const uint32_t boxA[3] = {SG_BK, SG_BM, 1}, boxB[3] = {SG_BK, (uint32_t)NTt, 1};
+      const uint32_t boxA[3] = {BKt, SG_BM, 1}, boxB[3] = {BKt, (uint32_t)NTt, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -500,7 +501,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.kind = PK_PAB; P.frag = idx;
       P.M = P.N = v; P.n_tile = NTt;
       P.tiles_m = (v + SG_BM - 1) / SG_BM; P.tiles_n = (v + NTt - 1) / NTt;
-      P.k0_blocks = (RL + SG_BK - 1) / SG_BK; P.k1_count = o;
+      P.k0_blocks = (RL + BKt - 1) / BKt; P.k1_count = o;
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
@@ -509,7 +510,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s4[3] = {(uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
-      const uint32_t boxA[4] = {SG_BK, SG_BM, 1, 1}, boxB[4] = {SG_BK, (uint32_t)NTt, 1, 1};
+      const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -520,7 +521,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.kind = PK_PIJ; P.frag = idx;
       P.M = P.N = o; P.n_tile = NTt;
       P.tiles_m = (o + SG_BM - 1) / SG_BM; P.tiles_n = (o + NTt - 1) / NTt;
-      P.k0_blocks = (vpad + SG_BK - 1) / SG_BK; P.k1_count = o * v;
+      P.k0_blocks = (vpad + BKt - 1) / BKt; P.k1_count = o * v;
       P.a_mode = P.b_mode = TM_5D; P.div5 = v;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
@@ -529,7 +530,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s5[4] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
-      const uint32_t boxA[5] = {SG_BK, 1, 1, SG_BM, 1}, boxB[5] = {SG_BK, 1, 1, (uint32_t)NTt, 1};
+      const uint32_t boxA[5] = {BKt, 1, 1, SG_BM, 1}, boxB[5] = {BKt, 1, 1, (uint32_t)NTt, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -542,7 +543,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.kind = PK_PIJ; P.frag = idx;
       P.M = P.N = o; P.n_tile = NTt;
       P.tiles_m = (o + SG_BM - 1) / SG_BM; P.tiles_n = (o + NTt - 1) / NTt;
-      P.k0_blocks = (vpad + SG_BK - 1) / SG_BK; P.k1_count = o * v;
+      P.k0_blocks = (vpad + BKt - 1) / BKt; P.k1_count = o * v;
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
@@ -551,7 +552,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
       const uint64_t s4[3] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, plane_b};
-      const uint32_t boxA[4] = {SG_BK, SG_BM, 1, 1}, boxB[4] = {SG_BK, (uint32_t)NTt, 1, 1};
+      const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;

@@ -11,11 +11,18 @@ using namespace rimp2;
 extern "C" int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t kpad,
                                         int32_t slices, const void* A, const void* B, double* C,
                                         void* stream) {
+  return rimp2_testing_slice_gemm_k(M, N, K, kpad, slices, 16, A, B, C, stream);
+}
+
+extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32_t kpad,
+                                          int32_t slices, int32_t stage_k, const void* A,
+                                          const void* B, double* C, void* stream) {
   if (M <= 0 || N <= 0 || K < 0 || kpad < K || kpad % 8 != 0 || slices < 2 || slices > 8 ||
       !A || !B || !C)
     return RIMP2_ERR_BAD_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const SplitLaunch cfg = split_launch_config(slices);
+  if (stage_k != 16 && stage_k != 32) return RIMP2_ERR_BAD_ARG;
+  const SplitLaunch cfg = split_launch_config(slices, stage_k, 0);
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   SplitProb P;
   memset(&P, 0, sizeof(P));
@@ -23,7 +30,7 @@ extern "C" int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t
   P.M = M; P.N = N; P.n_tile = cfg.n_tile_max;
   P.tiles_m = (M + SG_BM - 1) / SG_BM;
   P.tiles_n = (N + cfg.n_tile_max - 1) / cfg.n_tile_max;
-  P.ksplit = 1; P.k0_blocks = (K + SG_BK - 1) / SG_BK; P.k1_count = 1; P.k1_chunk = 1;
+  P.ksplit = 1; P.k0_blocks = (K + cfg.bk - 1) / cfg.bk; P.k1_count = 1; P.k1_chunk = 1;
   P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
   P.ea_rows = P.eb_rows = 0;
   P.ea_off = sizeof(SplitProb); P.eb_off = sizeof(SplitProb);   // int 8 stored there
@@ -33,7 +40,7 @@ extern "C" int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t
   const uint64_t sA[2] = {(uint64_t)kpad * 2, (uint64_t)M * kpad * 2};
   const uint64_t dB[3] = {(uint64_t)(K > 0 ? K : 1), (uint64_t)N, (uint64_t)slices};
   const uint64_t sB[2] = {(uint64_t)kpad * 2, (uint64_t)N * kpad * 2};
-  const uint32_t boxA[3] = {SG_BK, SG_BM, 1}, boxB[3] = {SG_BK, (uint32_t)cfg.n_tile_max, 1};
+  const uint32_t boxA[3] = {(uint32_t)cfg.bk, SG_BM, 1}, boxB[3] = {(uint32_t)cfg.bk, (uint32_t)cfg.n_tile_max, 1};
   if (encode_tmap(&P.tmA, A, 3, dA, sA, boxA) != RIMP2_OK ||
       encode_tmap(&P.tmB, B, 3, dB, sB, boxB) != RIMP2_OK)
     return RIMP2_ERR_UNSUPPORTED;

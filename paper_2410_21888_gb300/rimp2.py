@@ -59,7 +59,8 @@ class Options(ctypes.Structure):
     _fields_ = [("slices_v", ctypes.c_int32), ("slices_t", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("profile_stages", ctypes.c_int32),
-                ("max_workspace_bytes", ctypes.c_size_t), ("autotune_cache", ctypes.c_char_p)]
+                ("max_workspace_bytes", ctypes.c_size_t), ("stage_k", ctypes.c_int32),
+                ("n_tile", ctypes.c_int32), ("autotune_cache", ctypes.c_char_p)]
 
 
 class Stats(ctypes.Structure):
@@ -144,7 +145,7 @@ class Plan:
                  slices_t: int = 6, use_graph: bool = True, check_inputs: bool = True,
                  max_workspace_bytes: int = 0, profile_stages: bool = False,
                  want_gamma: bool = True, want_p: bool = True, autotune: bool = False,
-                 autotune_cache: str | None = None):
+                 autotune_cache: str | None = None, stage_k: int = 0, n_tile: int = 0):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -160,6 +161,8 @@ class Plan:
         opt.max_workspace_bytes = int(max_workspace_bytes)
         opt.profile_stages = int(profile_stages)
         opt.autotune = int(autotune)
+        opt.stage_k = int(stage_k)
+        opt.n_tile = int(n_tile)
         self._cache = autotune_cache.encode() if autotune_cache else None
         opt.autotune_cache = self._cache
         h = ctypes.c_void_p()

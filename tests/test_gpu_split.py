@@ -3,8 +3,9 @@
 1. The tensor-core slice GEMM alone against exact integer arithmetic: digits in
    [-128, 128], level sums 2^(-8(p+q)) sum_k A_p B_q for p + q < s.  Levels 0 and 1 of
    each 512-long K chunk are exact integers in FP32 (higher levels too unless a partial
-   sum passes 2^24); the chunks are combined in double-float, so the result matches the
-   exact value to ~2^-44 of the chunk level magnitudes.
+   sum passes 2^24); levels 0..2 are folded into a double-float accumulator exactly,
+   levels >= 3 in FP32, so the result matches the exact value to ~2^-46 of the absolute
+   digit products.
 2. Fragments through rimp2_energy_grad(precision=BF16_SPLIT) against the FP64 oracle.
    Tolerances: energy within 1e-8 Eh per fragment; Gamma, P_ij, P_ab, pair energies
    within 1e-9 relative Frobenius (the accuracy target of the split path).
@@ -32,29 +33,34 @@ def rel(a, b):
 
 def _hook():
     lib = rimp2.load()
-    f = lib.rimp2_testing_slice_gemm
-    f.argtypes = [ctypes.c_int32] * 5 + [ctypes.c_void_p] * 4
+    f = lib.rimp2_testing_slice_gemm_k
+    f.argtypes = [ctypes.c_int32] * 6 + [ctypes.c_void_p] * 4
     f.restype = ctypes.c_int
     return f
 
 
 def _exact_levels(A, B, s, chunk=512):
-    """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the sum over
-    512-long K chunks of |chunk level sums| (the magnitudes the kernel accumulates)."""
+    """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the magnitude
+    the kernel's rounding is relative to: sum over 512-long K chunks and levels of
+    2^(-8 l) sum_k |A_p||B_q| (the usual dot-product error model)."""
     M, N, K = A.shape[1], B.shape[1], A.shape[2]
     out = np.zeros((M, N))
     mag = np.zeros((M, N))
     for k0 in range(0, max(K, 1), chunk):
         for l in range(s):
             lev = np.zeros((M, N), dtype=np.int64)
+            lab = np.zeros((M, N), dtype=np.int64)
             for p in range(l + 1):
-                q = l - p
-                lev += A[p, :, k0:k0 + chunk].astype(np.int64) @ B[q, :, k0:k0 + chunk].astype(np.int64).T
+                a = A[p, :, k0:k0 + chunk].astype(np.int64)
+                b = B[l - p, :, k0:k0 + chunk].astype(np.int64)
+                lev += a @ b.T
+                lab += np.abs(a) @ np.abs(b).T
             out += lev.astype(np.float64) * 2.0 ** (-8 * l)
-            mag += np.abs(lev).astype(np.float64) * 2.0 ** (-8 * l)
+            mag += lab.astype(np.float64) * 2.0 ** (-8 * l)
     return out, mag
 
 
+@pytest.mark.parametrize("stage_k", [16, 32])
 @pytest.mark.parametrize("M,N,K,s,seed", [
     (128, 96, 64, 2, 0),
     (128, 96, 32, 5, 1),
@@ -65,7 +71,7 @@ def _exact_levels(A, B, s, chunk=512):
     (300, 260, 700, 6, 5),       # n_tile 80
     (129, 70, 257, 8, 6),        # n_tile 64, eight slices
 ])
-def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
+def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     rng = np.random.default_rng(seed)
     kpad = (K + 7) // 8 * 8
     A = rng.integers(-128, 129, size=(s, M, K))
@@ -79,14 +85,14 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
     Bd = torch.tensor(Bp, dtype=torch.bfloat16, device="cuda")
     assert torch.equal(Ad.float().cpu(), torch.tensor(Ap, dtype=torch.float32))
     C = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
-    rc = _hook()(M, N, K, kpad, s, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+    rc = _hook()(M, N, K, kpad, s, stage_k, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
                  torch.cuda.current_stream().cuda_stream)
     assert rc == 0
     ref, mag = _exact_levels(A, B, s)
     got = C.cpu().numpy()
     assert np.all(np.isfinite(got))
-    # an FP32 accumulator alone would give 2^-24, a wrong digit product at least 2^-14
-    # of the level-0 magnitude; demand double-float accuracy: 2^-44 of the chunk sums
+    # an FP32 accumulator alone would err by ~2^-24 of mag and one wrong integer in
+    # levels 0..2 by >= 2^-16 (absolute); demand 2^-44 of the absolute products
     bound = 2.0 ** -44 * (mag + 1.0)
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
 
@@ -109,10 +115,11 @@ def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
     ((5, 31, 1), 5),
     ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
 ])
-def test_split_fragment_parity(dims, seed):
+@pytest.mark.parametrize("stage_k", [16, 32])
+def test_split_fragment_parity(dims, seed, stage_k):
     f = synth.fragment_inputs(*dims, seed=seed)
     ref = oracle.fragment(f.B, f.eo, f.ev)
-    out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16")
+    out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=stage_k)
     check_split(out, ref)
 
 
