@@ -169,12 +169,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage-k", type=int, default=0, choices=[0, 16, 32],
                     help="K per tensor-core pipeline stage (0: library default)")
     ap.add_argument("--n-tile", type=int, default=0, choices=[0, 64, 80, 96])
-    ap.add_argument("--slices-t", type=int, default=6)
+    ap.add_argument("--slices-t", type=int, default=0, help="0: precision default (6 for bf16)")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the plain FP64 path reported beside the split path")
     args = ap.parse_args()
@@ -287,26 +287,29 @@ def main():
                 "kernel": "k_gemm_f64 (" + ("Gamma/P_ab/P_ij" if k == 3 else "V") + ")",
                 "peak_source": "measured DFMA peak (probes/dfma_peak.cu)"}
     else:
-        sv, stt = 5, args.slices_t
+        fp8 = head == "fp8"
+        sv, stt = (9, args.slices_t or 10) if fp8 else (5, args.slices_t or 6)
         prod_v, prod_t = sv * (sv + 1) // 2, stt * (stt + 1) // 2
         k = 3 if sm[3] >= sm[1] else 1
         Fk = F_c * prod_t if k == 3 else F_v * prod_v
         ach = Fk / (sm[k] * 1e-3) / 1e12
-        peak = float(peaks["bf16_tflops_sustained"])
+        # FP8 dense peak: the measured BF16 peak x the nominal FP8:BF16 ratio (4.5 / 2.25)
+        peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if fp8 else 1.0)
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get(k),
-                "kernel": "k_split_gemm (" + ("Gamma/P_ab/P_ij, 21 slice products"
-                                              if k == 3 else "V, 15 slice products") + ")",
-                "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)",
+                "kernel": "k_split_gemm (" + (f"Gamma/P_ab/P_ij, {prod_t} slice products"
+                                              if k == 3 else f"V, {prod_v} slice products") + ")",
+                "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)"
+                               + (" x 2 (nominal fp8:bf16)" if fp8 else ""),
                 "fp64_equivalent_tflops": (F_c if k == 3 else F_v) / (sm[k] * 1e-3) / 1e12}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": R["steps"], "warmup": R["warmup"], "ms_per_step": R["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "bf16",
+        "dtype": "f64" if head == "fp64" else head,
         "data": "synthetic",
-        "config": dict(WORKLOAD, precision=head if head == "fp64" else "bf16 split, 5 slices for V, "
-                                                                        "6 for Gamma/P",
+        "config": dict(WORKLOAD, precision=head if head == "fp64" else
+                       (f"{head} split, {sv} slices for V, {stt} for Gamma/P"),
                        l2="inputs larger than L2 (B 600 MB, workspace >> 129 MB); no flush",
                        fragments_per_s=ws * 1000.0 / R["ms"], energy_Eh=R["energy"]),
         "roofline": roof,

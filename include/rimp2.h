@@ -20,8 +20,9 @@
  *
  * Denominators, pair and cross-pair energy sums are FP64 in every precision mode.  In
  * RIMP2_FP64 every contraction is FP64.  In the split modes the four contractions (V,
- * Gamma, P_ab, P_ij) run on the tensor cores as sums of exact products of BF16 (or FP8)
- * integer slices accumulated in FP32 and recombined at higher precision.
+ * Gamma, P_ab, P_ij) run on the tensor cores as sums of exact products of integer
+ * digit slices (BF16: 8-bit digits; FP8 e4m3: 5-bit digits) accumulated in FP32 and
+ * recombined at higher precision.
  *
  * Layouts (all row-major, element offsets into caller-owned device pools):
  *   B[nocc][nvir][naux] FP64, naux fastest;  Gamma: same shape and layout as B;
@@ -65,7 +66,7 @@ extern "C" {
 typedef enum {
   RIMP2_FP64 = 0,        /* FP64 contractions (CUDA-core DFMA) */
   RIMP2_BF16_SPLIT = 1,  /* BF16 integer-slice products on tcgen05, FP32 accumulate */
-  RIMP2_FP8_SPLIT = 2    /* reserved: FP8 (e4m3) slices */
+  RIMP2_FP8_SPLIT = 2    /* FP8 (e4m3) integer-slice products on tcgen05, FP32 accumulate */
 } rimp2_precision;
 
 /* One fragment: sizes and element offsets into the batch pools.  An offset of -1
@@ -95,8 +96,14 @@ typedef struct rimp2_batch {
 } rimp2_batch;
 
 typedef struct rimp2_options {
-  int32_t slices_v;    /* split modes: slices of B for V (2..8, default 5)        */
-  int32_t slices_t;    /* split modes: slices for Gamma/P operands (2..8, default 6) */
+  int32_t slices_v;    /* split modes: digit slices of B for V; 0 = default (BF16: 5
+                          slices of 8 bits, range 2..8; FP8: 9 slices of 5 bits, 2..10).
+                          The first even level the truncated product triangle drops
+                          holds the squared middle digit of the diagonal V_ii(a,a), a
+                          one-signed error of 2^(-bits x that level): an odd count
+                          keeps it one level further down */
+  int32_t slices_t;    /* split modes: slices for the Gamma/P operands; 0 = default
+                          (BF16: 6, range 2..8; FP8: 10, range 2..10) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
   int32_t autotune;    /* 1: the first calls of the plan each run one variant of the

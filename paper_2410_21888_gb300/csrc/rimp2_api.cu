@@ -106,8 +106,8 @@ const char* rimp2_status_string(int s) {
 void rimp2_default_options(rimp2_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
-  opt->slices_v = 5;
-  opt->slices_t = 6;
+  opt->slices_v = 0;   // 0: the precision's default (BF16 5 / 6, FP8 8 / 10)
+  opt->slices_t = 0;
   opt->use_graph = 1;
   opt->check_inputs = 1;
   opt->autotune = 0;
@@ -424,14 +424,19 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   if (!out) return RIMP2_ERR_BAD_ARG;
   *out = nullptr;
   if (nfrag < 0 || (nfrag > 0 && !frags)) return RIMP2_ERR_BAD_ARG;
-  if (precision != RIMP2_FP64 && precision != RIMP2_BF16_SPLIT) return RIMP2_ERR_UNSUPPORTED;
+  if (precision != RIMP2_FP64 && precision != RIMP2_BF16_SPLIT && precision != RIMP2_FP8_SPLIT)
+    return RIMP2_ERR_UNSUPPORTED;
   int rc = check_frag_shapes(frags, nfrag);
   if (rc != RIMP2_OK) return rc;
   rimp2_options o;
   rimp2_default_options(&o);
   if (opt) o = *opt;
+  const bool fp8 = precision == RIMP2_FP8_SPLIT;
+  if (o.slices_v == 0) o.slices_v = fp8 ? 9 : 5;   // odd: see the header on slices_v
+  if (o.slices_t == 0) o.slices_t = fp8 ? 10 : 6;
+  const int smax = fp8 ? 10 : 8;   // levels x tile width must fit the 512 TMEM columns
   if (precision != RIMP2_FP64 &&
-      (o.slices_v < 2 || o.slices_v > 8 || o.slices_t < 2 || o.slices_t > 8 ||
+      (o.slices_v < 2 || o.slices_v > smax || o.slices_t < 2 || o.slices_t > smax ||
        (o.stage_k != 0 && o.stage_k != 16 && o.stage_k != 32) ||
        (o.n_tile != 0 && o.n_tile != 64 && o.n_tile != 80 && o.n_tile != 96)))
     return RIMP2_ERR_UNSUPPORTED;

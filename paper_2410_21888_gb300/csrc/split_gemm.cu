@@ -116,6 +116,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       : "memory");
 }
 
+__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -139,14 +149,13 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// UMMA shared-memory descriptor of a K-major operand whose rows hold BK bf16 (2 BK
-// bytes) with the matching swizzle: 8-row core groups 16 BK bytes apart (SBO),
-// descriptor version 1, layout SWIZZLE_64B (4) for 64-byte rows, SWIZZLE_32B (6) for
-// 32-byte rows.
-template <int BK>
+// UMMA shared-memory descriptor of a K-major operand with ROWB-byte rows (64 or 32)
+// and the matching swizzle: 8-row core groups 8 ROWB bytes apart (SBO), descriptor
+// version 1, layout SWIZZLE_64B (4) for 64-byte rows, SWIZZLE_32B (6) for 32-byte rows.
+template <int ROWB>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  constexpr uint64_t layout = BK == 32 ? 4u : 6u;
-  constexpr uint64_t sbo = (8u * 2u * BK) >> 4;
+  constexpr uint64_t layout = ROWB == 64 ? 4u : 6u;
+  constexpr uint64_t sbo = (8u * ROWB) >> 4;
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | (sbo << 32) |
          ((uint64_t)1u << 46) | (layout << 61);
 }
@@ -232,14 +241,20 @@ __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm,
 
 // ------------------------------------------------------------------ the kernel
 
-template <int NT, int BK>
+// F8 = false: BF16 digits (8 bits each, kind::f16); true: FP8 e4m3 digits (5 bits each,
+// kind::f8f6f4).  Both consume 32 bytes of K per MMA, so the tile geometry in bytes is
+// the same: ROWB bytes of K per row and pipeline stage.
+template <int NT, int ROWB, bool F8>
 __global__ void __launch_bounds__(SG_THREADS, 1)
 k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, Bases bs,
              unsigned* __restrict__ counter, int slices, int stages) {
   constexpr int NC = NT / 2;                 // columns per epilogue thread
-  constexpr uint32_t A_TILE = SG_BM * BK * 2;   // bytes of one 128 x BK bf16 tile
-  constexpr uint32_t B_TILE = NT * BK * 2;
-  constexpr int CHUNK_STAGES = SG_CHUNK_K / BK;
+  constexpr uint32_t A_TILE = SG_BM * ROWB;  // bytes of one 128-row tile
+  constexpr uint32_t B_TILE = NT * ROWB;
+  constexpr int BKE = F8 ? ROWB : ROWB / 2;  // K elements per stage
+  constexpr int CHUNK_STAGES = SG_CHUNK_K / BKE;
+  constexpr int LB = F8 ? 5 : 8;             // bits per digit
+  constexpr int EXACT = F8 ? 5 : 3;          // levels folded by error-free sums (LB*l < 24)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -309,7 +324,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           pending[st] = true;
           pend_ph[st] = ph;
           const int k1 = ti.k1b + kk / P->k0_blocks;
-          const int x = (kk % P->k0_blocks) * BK;
+          const int x = (kk % P->k0_blocks) * BKE;
           const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
           for (int p = 0; p < slices; ++p)
             tma_operand(base + p * A_TILE, &P->tmA, full + st, P->a_mode, x, rowA, k1, P->div5, p);
@@ -335,7 +350,8 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
     if (lane == 0) {
       // kind::f16 instruction descriptor without N: F32 accumulate, BF16 A and B, both
       // K-major, M = 128; N (a multiple of NT up to 256) is or-ed in per MMA
-      const uint32_t idesc_m = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SG_BM >> 4) << 24);
+      constexpr uint32_t kFmt = F8 ? 0u : 1u;   // E4M3 (kind::f8f6f4) or BF16 (kind::f16)
+      const uint32_t idesc_m = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(SG_BM >> 4) << 24);
       constexpr int kGroup = 256 / NT;
       uint32_t st = 0, ph = 0, te_count = 0;
       int tslot = 0;
@@ -360,18 +376,19 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             tc_fence_after();
             const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
 #pragma unroll
-            for (int k16 = 0; k16 < BK / 16; ++k16) {
+            for (int k16 = 0; k16 < ROWB / 32; ++k16) {
               for (int p = 0; p < slices; ++p) {
-                const uint64_t adesc = smem_desc<BK>(base + p * A_TILE) + (uint64_t)(k16 * 2);
+                const uint64_t adesc = smem_desc<ROWB>(base + p * A_TILE) + (uint64_t)(k16 * 2);
                 // one MMA of A_p against the contiguous B tiles q0 .. q0+nq-1: the column
                 // block of B_q lands on the level-(p+q) accumulator at (p+q) * NT
                 for (int q0 = 0; q0 + p < slices; q0 += kGroup) {
                   const int nq = min(kGroup, slices - p - q0);
                   const uint64_t bdesc =
-                      smem_desc<BK>(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
+                      smem_desc<ROWB>(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
                   const uint32_t acc = (kk == c * CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
-                  umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc,
-                            idesc_m | ((uint32_t)((nq * NT) >> 3) << 17), acc);
+                  const uint32_t idesc = idesc_m | ((uint32_t)((nq * NT) >> 3) << 17);
+                  if (F8) umma_f8(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
+                  else umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
                 }
               }
             }
@@ -413,16 +430,16 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
         if (!mbar_wait(tmem_full, tf_count & 1u, abort_flag)) { ok = false; break; }
         ++tf_count;
         tc_fence_after();
-        // Levels 0..2 are folded into (hi, lo) by error-free sums; levels >= 3 carry at
-        // most 2^-24 of the value and are accumulated into lo directly (FMA).
+        // Levels l < EXACT are folded into (hi, lo) by error-free sums; higher levels
+        // carry at most 2^-24 of the value and are accumulated into lo directly (FMA).
         for (int l = slices - 1; l >= 0; --l) {
           float v[NC];
 #pragma unroll
           for (int g = 0; g < NC / 8; ++g)
             tmem_ld8(lane_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
           tmem_wait_ld();
-          const float sc = __int_as_float((127 - 8 * l) << 23);   // 2^(-8 l)
-          if (l >= 3) {
+          const float sc = __int_as_float((127 - LB * l) << 23);   // 2^(-LB l)
+          if (l >= EXACT) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc_l[c] = fmaf(v[c], sc, acc_l[c]);
           } else {
@@ -466,7 +483,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             const int n = nbase + c;
             if (n >= P->N) continue;
             float s1, s2;
-            pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 16, s1, s2);
+            pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB, s1, s2);
             const df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
             const float2 dn = dv[n];
             const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
@@ -485,7 +502,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           for (int c = 0; c < NC; ++c) {
             const int n = nbase + c;
             if (n >= P->N) continue;
-            const int e = ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 16;
+            const int e = ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB;
             const double val = ldexp((double)acc_h[c] + (double)acc_l[c], e);
             if ((P->kind == PK_GAMMA || P->kind == PK_RAW) && P->ksplit == 1)
               C[(long long)m * P->ldc + n] = P->alpha * val;
@@ -514,13 +531,20 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
 
 // ------------------------------------------------------------------ host side
 
-SplitLaunch split_launch_config(int slices, int bk, int n_tile) {
+SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   SplitLaunch c{};
   c.slices = slices;
-  c.bk = bk == 16 ? 16 : 32;
-  const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
-  c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : widest;
-  const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * c.bk * 2;
+  c.fp8 = fp8;
+  if (fp8) {
+    c.bk = 64;                       // 64 one-byte elements per 64-byte row
+    c.n_tile_max = slices <= 8 ? 64 : 48;
+  } else {
+    c.bk = bk == 16 ? 16 : 32;
+    const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
+    c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : widest;
+  }
+  const size_t rowb = fp8 ? 64 : (size_t)c.bk * 2;
+  const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * rowb;
   const size_t budget = 227 * 1024 - 1024 - 256;
   int st = (int)(budget / stage);
   if (st > 8) st = 8;
@@ -530,11 +554,11 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile) {
   return c;
 }
 
-template <int NT, int BK>
+template <int NT, int ROWB, bool F8>
 static cudaError_t launch_nt(const SplitProb* d_probs, int nprobs, long long total, Bases bs,
                              unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
-  k_split_gemm<NT, BK><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs, counter,
-                                                         cfg.slices, cfg.stages);
+  k_split_gemm<NT, ROWB, F8><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs,
+                                                               counter, cfg.slices, cfg.stages);
   return cudaGetLastError();
 }
 
@@ -542,12 +566,13 @@ static cudaError_t launch_nt(const SplitProb* d_probs, int nprobs, long long tot
 cudaError_t split_gemm_prepare() {
   const int bytes = 227 * 1024;
   cudaError_t e = cudaSuccess;
-#define RIMP2_PREP(NT, BK)                                                                  \
+#define RIMP2_PREP(NT, ROWB, F8)                                                            \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_split_gemm<NT, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             bytes);
-  RIMP2_PREP(96, 32) RIMP2_PREP(80, 32) RIMP2_PREP(64, 32)
-  RIMP2_PREP(96, 16) RIMP2_PREP(80, 16) RIMP2_PREP(64, 16)
+    e = cudaFuncSetAttribute(k_split_gemm<NT, ROWB, F8>,                                     \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  RIMP2_PREP(96, 64, false) RIMP2_PREP(80, 64, false) RIMP2_PREP(64, 64, false)
+  RIMP2_PREP(96, 32, false) RIMP2_PREP(80, 32, false) RIMP2_PREP(64, 32, false)
+  RIMP2_PREP(64, 64, true) RIMP2_PREP(48, 64, true)
 #undef RIMP2_PREP
   return e;
 }
@@ -555,18 +580,22 @@ cudaError_t split_gemm_prepare() {
 cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles, Bases bs,
                               unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
-  const long long g = total_tiles < grid ? total_tiles : grid;
+  const int g = (int)(total_tiles < grid ? total_tiles : grid);
+  if (cfg.fp8) {
+    if (cfg.n_tile_max == 64) return launch_nt<64, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    return launch_nt<48, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+  }
   if (cfg.bk == 32) {
     switch (cfg.n_tile_max) {
-      case 96: return launch_nt<96, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-      case 80: return launch_nt<80, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-      default: return launch_nt<64, 32>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+      case 96: return launch_nt<96, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+      case 80: return launch_nt<80, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+      default: return launch_nt<64, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
     }
   }
   switch (cfg.n_tile_max) {
-    case 96: return launch_nt<96, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-    case 80: return launch_nt<80, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
-    default: return launch_nt<64, 16>(d_probs, nprobs, total_tiles, bs, counter, cfg, (int)g, s);
+    case 96: return launch_nt<96, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    case 80: return launch_nt<80, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    default: return launch_nt<64, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
 }
 
@@ -578,7 +607,7 @@ int split_gemm_grid() {
 }
 
 int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
-                const uint64_t* strides_bytes, const uint32_t* box) {
+                const uint64_t* strides_bytes, const uint32_t* box, int elem_bytes) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -597,9 +626,13 @@ int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dim
     es[i] = 1;
     if (i > 0) s[i - 1] = strides_bytes[i - 1];
   }
-  if (box[0] != 16 && box[0] != 32) return RIMP2_ERR_UNSUPPORTED;
-  const CUtensorMapSwizzle sw = box[0] == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
-  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
+  const unsigned row_bytes = box[0] * (unsigned)elem_bytes;
+  if ((elem_bytes != 1 && elem_bytes != 2) || (row_bytes != 32 && row_bytes != 64))
+    return RIMP2_ERR_UNSUPPORTED;
+  const CUtensorMapSwizzle sw = row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+  const CUtensorMapDataType dt =
+      elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUresult r = fn(tm, dt, (cuuint32_t)rank, const_cast<void*>(base),
                         d, s, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? RIMP2_OK : RIMP2_ERR_UNSUPPORTED;

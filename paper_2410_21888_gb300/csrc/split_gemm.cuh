@@ -2,7 +2,10 @@
 //
 // Operands are "slices": balanced base-256 integer digits d_p in [-128, 128] of FP64
 // values relative to a power-of-two scale, stored as BF16 (exact for such integers):
-//   x ~= sum_p d_p 2^(E - 8(p+1)),   |x| < 2^(E-1).
+//   x ~= sum_p d_p 2^(E - 8(p+1)),   |x| < 2^(E-1),
+// or (FP8 mode) balanced base-32 digits in [-16, 16] stored as e4m3 (exact), with 5 in
+// place of 8 in every formula below; then |digit product| <= 2^8 and every level sum of
+// a 512-long chunk is an exact integer.
 // C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 16) sum_l 2^(-8 l) S_l with
 // S_l = sum_{p+q=l} sum_k dA_p dB_q, the truncated level sum kept for l < s.  Each S_l
 // accumulates in its own FP32 TMEM accumulator over K chunks of 512, where levels 0
@@ -65,7 +68,8 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
 
 struct SplitLaunch {
   int slices;     // s (levels); same for every problem of one launch
-  int bk;         // K elements per pipeline stage (16 or 32)
+  int bk;         // K elements per pipeline stage (BF16: 16 or 32; FP8: 64)
+  bool fp8;       // digits as FP8 e4m3 (5 bits, kind::f8f6f4) instead of BF16 (8 bits)
   int n_tile_max; // widest n_tile of the launch (smem layout)
   int stages;     // pipeline depth
   size_t smem;    // dynamic shared memory bytes
@@ -73,7 +77,7 @@ struct SplitLaunch {
 
 // n_tile: columns per level accumulator (0: widest that fits 512 TMEM columns; else 64,
 // 80 or 96, capped by the TMEM budget)
-SplitLaunch split_launch_config(int slices, int bk = 32, int n_tile = 0);
+SplitLaunch split_launch_config(int slices, int bk = 32, int n_tile = 0, bool fp8 = false);
 cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles,
                               Bases bs, unsigned* counter, const SplitLaunch& cfg, int grid,
                               cudaStream_t s);
@@ -81,8 +85,9 @@ int split_gemm_grid();
 cudaError_t split_gemm_prepare();
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-// box[0] must equal bk (16 -> 32B swizzle, 32 -> 64B swizzle)
+// box[0] x elem_bytes must be 32 (32B swizzle) or 64 (64B swizzle); elem_bytes 2 = BF16,
+// 1 = raw bytes (FP8 digits)
 int encode_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
-                const uint64_t* strides_bytes, const uint32_t* box);
+                const uint64_t* strides_bytes, const uint32_t* box, int elem_bytes);
 
 }  // namespace rimp2

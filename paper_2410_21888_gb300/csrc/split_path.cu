@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "split_path.cuh"
 
@@ -79,34 +80,52 @@ __device__ __forceinline__ void tri_rc(long long t, int& r, int& c) {
   r = (int)(t - cc * (cc + 1) / 2);
 }
 
-__device__ __forceinline__ __nv_bfloat16 digit_bf16(float d) { return __float2bfloat16_rn(d); }
+// One digit (an integer in [-2^(LB-1), 2^(LB-1)]) in the slice format: BF16 (LB = 8)
+// or FP8 e4m3 (LB = 5); both represent these integers exactly.
+template <bool F8> struct Digit;
+template <> struct Digit<false> {
+  using T = __nv_bfloat16;
+  static constexpr int LB = 8;
+  __device__ static T enc(float d) { return __float2bfloat16_rn(d); }
+};
+template <> struct Digit<true> {
+  using T = unsigned char;
+  static constexpr int LB = 5;
+  __device__ static T enc(float d) {
+    return (T)__nv_cvt_float_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
+  }
+};
 
-// Digits of an FP64 value x relative to 2^E (|x| < 2^(E-1)): X = x 2^(8-E),
-// d_p = rint(X), X <- 256 (X - d_p); every step is exact in FP64.
-__device__ __forceinline__ void digits_f64(double x, int E, int s, __nv_bfloat16* out,
+// Digits of an FP64 value x relative to 2^E (|x| <= 2^(E-1)): X = x 2^(LB-E),
+// d_p = rint(X), X <- 2^LB (X - d_p); every step is exact in FP64.
+template <bool F8>
+__device__ __forceinline__ void digits_f64(double x, int E, int s, typename Digit<F8>::T* out,
                                            long long plane) {
-  double X = ldexp(x, 8 - E);
+  constexpr int LB = Digit<F8>::LB;
+  double X = ldexp(x, LB - E);
   for (int p = 0; p < s; ++p) {
     const double d = rint(X);
-    out[p * plane] = digit_bf16((float)d);
-    X = (X - d) * 256.0;
+    out[p * plane] = Digit<F8>::enc((float)d);
+    X = (X - d) * (double)(1 << LB);
   }
 }
 
 // Same for a double-float (h, l): d_p = rint(X_h); the remainder (X_h - d_p) is exact and
-// is re-joined with X_l by an error-free sum before the next scaling by 256.
-__device__ __forceinline__ void digits_df(dfl x, int E, int s, __nv_bfloat16* out,
+// is re-joined with X_l by an error-free sum before the next scaling by 2^LB.
+template <bool F8>
+__device__ __forceinline__ void digits_df(dfl x, int E, int s, typename Digit<F8>::T* out,
                                           long long plane) {
-  const int e = max(-252, min(254, 8 - E));
+  constexpr int LB = Digit<F8>::LB;
+  const int e = max(-252, min(254, LB - E));
   const int e1 = e / 2, e2 = e - e1;
   const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
   float xh = (x.h * s1) * s2, xl = (x.l * s1) * s2;
   for (int p = 0; p < s; ++p) {
     const float d = rintf(xh);
-    out[p * plane] = digit_bf16(d);
+    out[p * plane] = Digit<F8>::enc(d);
     const dfl r = d_two_sum(xh - d, xl);
-    xh = r.h * 256.f;
-    xl = r.l * 256.f;
+    xh = r.h * (float)(1 << LB);
+    xl = r.l * (float)(1 << LB);
   }
 }
 
@@ -122,8 +141,10 @@ __global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases b
 
 // One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, and the
 // fragment-wide maximum exponent used by the Gamma operand.
+template <bool F8>
 __global__ void __launch_bounds__(256)
 k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, Bases bs) {
+  using DT = typename Digit<F8>::T;
   const long long gr = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (gr >= rows) return;
@@ -137,8 +158,8 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
   const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
   char* ws = (char*)bs.ws;
   const long long plane = (long long)F.o * F.v * F.xpad;
-  __nv_bfloat16* out = (__nv_bfloat16*)(ws + F.bs1) + (long long)r * F.xpad;
-  for (int q = lane; q < F.X; q += 32) digits_f64(x[q], E, sv, out + q, plane);
+  DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
+  for (int q = lane; q < F.X; q += 32) digits_f64<F8>(x[q], E, sv, out + q, plane);
   if (lane == 0) {
     ((int*)(ws + F.erow))[r] = E;
     const int i = r / F.v, a = r - i * F.v;
@@ -150,8 +171,10 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
 
 // Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale per
 // fragment.  32 x 32 tiles transposed through shared memory.
+template <bool F8>
 __global__ void __launch_bounds__(256)
 k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
+  using DT = typename Digit<F8>::T;
   __shared__ double tile[32][33];
   const long long gt = blockIdx.x;
   const SplitFragDev& F = f[find_sfd(f, nf, gt, 1)];
@@ -174,18 +197,20 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   char* ws = (char*)bs.ws;
   const int E = *(const int*)(ws + F.scal);
   const long long plane = (long long)F.X * RL;
-  __nv_bfloat16* out = (__nv_bfloat16*)(ws + F.bs2);
+  DT* out = (DT*)(ws + F.bs2);
   for (int r = ty; r < 32; r += 8) {
     const int Q = tq * 32 + r, c = tc * 32 + tx;
-    if (Q < F.X && c < RL) digits_f64(tile[tx][r], E, st, out + (long long)Q * RL + c, plane);
+    if (Q < F.X && c < RL) digits_f64<F8>(tile[tx][r], E, st, out + (long long)Q * RL + c, plane);
   }
 }
 
 // One CTA per pair block (i <= j): reads T_ij from the double-float planes, writes the
 // digits of Tt and T for the (i,j) block and, if i != j, the (j,i) block, zeroes the
 // row padding, and stores the pair energy e_ij = sum_ab Tt_ij(a,b) T_ij(a,b) D_ijab.
+template <bool F8>
 __global__ void __launch_bounds__(256)
 k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
+  using DT = typename Digit<F8>::T;
   __shared__ float Xh[32][33], Xl[32][33], Yh[32][33], Yl[32][33];
   // per tile pair: r_a = (e_i + e_j) - e_a for rows and e_b for columns, as double-floats
   // (formed once per row/column in FP64, so the inner loops stay in FP32)
@@ -205,8 +230,8 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const float* Tl = (const float*)(ws + F.tlo);
   const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
   const int E_T = (int)emax - 124, E_Tt = (int)emax - 123;
-  __nv_bfloat16* tts = (__nv_bfloat16*)(ws + F.tts);
-  __nv_bfloat16* ts = (__nv_bfloat16*)(ws + F.ts);
+  DT* tts = (DT*)(ws + F.tts);
+  DT* ts = (DT*)(ws + F.ts);
   const long long plane = ov * RL;
   const double* eo = bs.eps + F.eo_off;
   const double* ev = bs.eps + F.ev_off;
@@ -219,8 +244,8 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 
   auto put = [&](long long row, int col, dfl t, dfl tt) {
     const long long o_ = row * RL + col;
-    digits_df(t, E_T, st, ts + o_, plane);
-    digits_df(tt, E_Tt, st, tts + o_, plane);
+    digits_df<F8>(t, E_T, st, ts + o_, plane);
+    digits_df<F8>(tt, E_Tt, st, tts + o_, plane);
   };
 
   for (long long q = 0; q < npairs; ++q) {
@@ -304,7 +329,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   // zero the padding columns b in [v, vpad) of this block's rows
   const int npad = F.vpad - v;
   if (npad > 0) {
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    const DT z = Digit<F8>::enc(0.f);
     for (int e = tid; e < v * npad; e += blockDim.x) {
       const int a = e / npad, b = v + e % npad;
       for (int p = 0; p < st; ++p) {
@@ -341,8 +366,9 @@ int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.precision = precision;
   sp.slices_v = opt.slices_v;
   sp.slices_t = opt.slices_t;
-  sp.cfg_v = split_launch_config(sp.slices_v, opt.stage_k ? opt.stage_k : 32, opt.n_tile);
-  sp.cfg_t = split_launch_config(sp.slices_t, opt.stage_k ? opt.stage_k : 32, opt.n_tile);
+  sp.fp8 = precision == RIMP2_FP8_SPLIT;
+  sp.cfg_v = split_launch_config(sp.slices_v, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
+  sp.cfg_t = split_launch_config(sp.slices_t, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
   sp.grid = split_gemm_grid();
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   sp.ready = true;
@@ -357,23 +383,28 @@ struct Layout {
   size_t bs1, bs2, erow, drow, thi, tlo, tts, ts, ep, scal, total;
 };
 
+// element size of the digit planes and the padding that keeps every row 16-byte aligned
+size_t esz_of(const SplitPlan& sp) { return sp.fp8 ? 1 : 2; }
+int padg(const SplitPlan& sp) { return sp.fp8 ? 16 : 8; }
+
 Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   const size_t o = f.nocc, v = f.nvir, X = f.naux;
-  const size_t ov = o * v, vpad = rup((int)v, 8), xpad = rup((int)X, 8), RL = o * vpad;
+  const size_t esz = esz_of(sp);
+  const size_t ov = o * v, vpad = rup((int)v, padg(sp)), xpad = rup((int)X, padg(sp)), RL = o * vpad;
   // digit planes of T / Tt (and B for Gamma) exist only when an output needs them
   const bool want_t = f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0;
   const size_t st_t = want_t ? (size_t)sp.slices_t : 0;
   const size_t st_g = f.gamma_off >= 0 ? (size_t)sp.slices_t : 0;
   Layout L{};
   size_t off = 0;
-  L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * 2);
-  L.bs2 = off; off += al256(st_g * X * RL * 2);
+  L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * esz);
+  L.bs2 = off; off += al256(st_g * X * RL * esz);
   L.erow = off; off += al256(ov * 4);
   L.drow = off; off += al256(ov * 8);
   L.thi = off; off += al256(ov * ov * 4);
   L.tlo = off; off += al256(ov * ov * 4);
-  L.tts = off; off += al256(st_t * ov * RL * 2);
-  L.ts = off; off += al256(st_t * ov * RL * 2);
+  L.tts = off; off += al256(st_t * ov * RL * esz);
+  L.ts = off; off += al256(st_t * ov * RL * esz);
   L.ep = off; off += al256(o * o * 8);
   L.scal = off; off += 256;
   L.total = off;
@@ -424,7 +455,8 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     const rimp2_frag& f = frags[idx];
     const Layout L = frag_layout(sp, f);
     const int o = f.nocc, v = f.nvir, X = f.naux;
-    const int ov = o * v, vpad = rup(v, 8), xpad = rup(X, 8), RL = o * vpad;
+    const int ov = o * v, vpad = rup(v, padg(sp)), xpad = rup(X, padg(sp)), RL = o * vpad;
+    const uint64_t E2 = esz_of(sp);
     SplitFragDev s{};
     s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
     s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
@@ -467,14 +499,14 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.d_off = s.drow; P.et_off = s.scal + 4; P.v = v;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
-      const uint64_t str[2] = {(uint64_t)xpad * 2, (uint64_t)ov * xpad * 2};
+      const uint64_t str[2] = {(uint64_t)xpad * E2, (uint64_t)ov * xpad * E2};
       const uint32_t boxA[3] = {BKv, SG_BM, 1}, boxB[3] = {BKv, (uint32_t)NTv, 1};
-      if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA) != RIMP2_OK ||
-          encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB) != RIMP2_OK)
+      if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA, (int)E2) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_v.push_back(P);
     }
-    const uint64_t plane_b = (uint64_t)ov * RL * 2;
+    const uint64_t plane_b = (uint64_t)ov * RL * E2;
     if (g) {  // Gamma[(i,a)][Q] = sum_(j,b) Tt[(i,a)][(j,b)] B[(j,b)][Q]
       SplitProb P{};
       P.kind = PK_GAMMA; P.frag = idx;
@@ -487,12 +519,12 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)st};
-      const uint64_t sA[2] = {(uint64_t)RL * 2, plane_b};
+      const uint64_t sA[2] = {(uint64_t)RL * E2, plane_b};
       const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
-      const uint64_t sB[2] = {(uint64_t)RL * 2, (uint64_t)X * RL * 2};
+      const uint64_t sB[2] = {(uint64_t)RL * E2, (uint64_t)X * RL * E2};
       const uint32_t boxA[3] = {BKt, SG_BM, 1}, boxB[3] = {BKt, (uint32_t)NTt, 1};
-      if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA) != RIMP2_OK ||
-          encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB) != RIMP2_OK)
+      if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA, (int)E2) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     }
@@ -509,10 +541,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
-      const uint64_t s4[3] = {(uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
+      const uint64_t s4[3] = {(uint64_t)RL * E2, (uint64_t)v * RL * E2, plane_b};
       const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
-      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
-          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
+      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     }
@@ -529,10 +561,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
-      const uint64_t s5[4] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, (uint64_t)v * RL * 2, plane_b};
+      const uint64_t s5[4] = {(uint64_t)vpad * E2, (uint64_t)RL * E2, (uint64_t)v * RL * E2, plane_b};
       const uint32_t boxA[5] = {BKt, 1, 1, SG_BM, 1}, boxB[5] = {BKt, 1, 1, (uint32_t)NTt, 1};
-      if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA) != RIMP2_OK ||
-          encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB) != RIMP2_OK)
+      if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA, (int)E2) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     } else if (f.pij_off >= 0) {
@@ -551,10 +583,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
-      const uint64_t s4[3] = {(uint64_t)vpad * 2, (uint64_t)RL * 2, plane_b};
+      const uint64_t s4[3] = {(uint64_t)vpad * E2, (uint64_t)RL * E2, plane_b};
       const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
-      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA) != RIMP2_OK ||
-          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB) != RIMP2_OK)
+      if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
+          encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_c.push_back(P);
     }
@@ -591,12 +623,14 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   ++nl;
   e = cudaGetLastError();
   if (e == cudaSuccess && w.rows > 0) {
-    k_slice_b1<<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
+    if (sp.fp8) k_slice_b1<true><<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
+    else k_slice_b1<false><<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
     ++nl;
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && w.b2_tiles > 0) {
-    k_slice_b2<<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    if (sp.fp8) k_slice_b2<true><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    else k_slice_b2<false><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
     ++nl;
     e = cudaGetLastError();
   }
@@ -608,7 +642,8 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   }
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
   if (e == cudaSuccess && total_pairs > 0) {
-    k_amp_split<<<(unsigned)total_pairs, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    if (sp.fp8) k_amp_split<true><<<(unsigned)total_pairs, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    else k_amp_split<false><<<(unsigned)total_pairs, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
     ++nl;
     e = cudaGetLastError();
   }

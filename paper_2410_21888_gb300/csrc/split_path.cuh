@@ -31,6 +31,7 @@ struct SplitPlan {
   SplitLaunch cfg_v{}, cfg_t{};
   int grid = 0;
   bool ready = false;
+  bool fp8 = false;  // RIMP2_FP8_SPLIT: e4m3 digits
   int variant = 0;   // contraction-stage variant (autotuner), see split_variant_desc
 };
 

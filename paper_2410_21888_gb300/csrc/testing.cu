@@ -11,18 +11,21 @@ using namespace rimp2;
 extern "C" int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t kpad,
                                         int32_t slices, const void* A, const void* B, double* C,
                                         void* stream) {
-  return rimp2_testing_slice_gemm_k(M, N, K, kpad, slices, 16, A, B, C, stream);
+  return rimp2_testing_slice_gemm_k(M, N, K, kpad, slices, 32, 0, A, B, C, stream);
 }
 
 extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32_t kpad,
-                                          int32_t slices, int32_t stage_k, const void* A,
-                                          const void* B, double* C, void* stream) {
-  if (M <= 0 || N <= 0 || K < 0 || kpad < K || kpad % 8 != 0 || slices < 2 || slices > 8 ||
-      !A || !B || !C)
+                                          int32_t slices, int32_t stage_k, int32_t fp8,
+                                          const void* A, const void* B, double* C,
+                                          void* stream) {
+  if (M <= 0 || N <= 0 || K < 0 || kpad < K || kpad % (fp8 ? 16 : 8) != 0 || slices < 2 ||
+      slices > (fp8 ? 10 : 8) || !A || !B || !C)
     return RIMP2_ERR_BAD_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (stage_k != 16 && stage_k != 32) return RIMP2_ERR_BAD_ARG;
-  const SplitLaunch cfg = split_launch_config(slices, stage_k, 0);
+  if (!fp8 && stage_k != 16 && stage_k != 32) return RIMP2_ERR_BAD_ARG;
+  const SplitLaunch cfg = split_launch_config(slices, stage_k, 0, fp8 != 0);
+  const int E8 = fp8 ? 5 : 8;        // EA = EB = bits per digit: product scale 2^0
+  const int esz = fp8 ? 1 : 2;
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   SplitProb P;
   memset(&P, 0, sizeof(P));
@@ -37,12 +40,12 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
   P.c_off = 0; P.ldc = N; P.alpha = 1.0;
   P.ntiles = (long long)P.tiles_m * P.tiles_n;
   const uint64_t dA[3] = {(uint64_t)(K > 0 ? K : 1), (uint64_t)M, (uint64_t)slices};
-  const uint64_t sA[2] = {(uint64_t)kpad * 2, (uint64_t)M * kpad * 2};
+  const uint64_t sA[2] = {(uint64_t)kpad * esz, (uint64_t)M * kpad * esz};
   const uint64_t dB[3] = {(uint64_t)(K > 0 ? K : 1), (uint64_t)N, (uint64_t)slices};
-  const uint64_t sB[2] = {(uint64_t)kpad * 2, (uint64_t)N * kpad * 2};
+  const uint64_t sB[2] = {(uint64_t)kpad * esz, (uint64_t)N * kpad * esz};
   const uint32_t boxA[3] = {(uint32_t)cfg.bk, SG_BM, 1}, boxB[3] = {(uint32_t)cfg.bk, (uint32_t)cfg.n_tile_max, 1};
-  if (encode_tmap(&P.tmA, A, 3, dA, sA, boxA) != RIMP2_OK ||
-      encode_tmap(&P.tmB, B, 3, dB, sB, boxB) != RIMP2_OK)
+  if (encode_tmap(&P.tmA, A, 3, dA, sA, boxA, esz) != RIMP2_OK ||
+      encode_tmap(&P.tmB, B, 3, dB, sB, boxB, esz) != RIMP2_OK)
     return RIMP2_ERR_UNSUPPORTED;
   const size_t bytes = sizeof(SplitProb) + 256;
   char* buf = nullptr;
@@ -50,8 +53,7 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
   char host[sizeof(SplitProb) + 256];
   memset(host, 0, sizeof(host));
   memcpy(host, &P, sizeof(P));
-  const int eight = 8;
-  memcpy(host + sizeof(SplitProb), &eight, sizeof(int));   // EA = EB = 8: scale 2^0
+  memcpy(host + sizeof(SplitProb), &E8, sizeof(int));   // EA + EB - 2 bits = 0
   int rc = RIMP2_OK;
   unsigned* counter = (unsigned*)(buf + sizeof(SplitProb) + 64);
   unsigned* status = (unsigned*)(buf + sizeof(SplitProb) + 128);

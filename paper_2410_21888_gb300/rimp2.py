@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(HERE, "_build", "librimp2.so")
 
 RIMP2_FP64 = 0
 RIMP2_BF16_SPLIT = 1
-PRECISIONS = {"fp64": RIMP2_FP64, "bf16": RIMP2_BF16_SPLIT, "bf16_split": RIMP2_BF16_SPLIT}
+RIMP2_FP8_SPLIT = 2
+PRECISIONS = {"fp64": RIMP2_FP64, "bf16": RIMP2_BF16_SPLIT, "bf16_split": RIMP2_BF16_SPLIT,
+              "fp8": RIMP2_FP8_SPLIT, "fp8_split": RIMP2_FP8_SPLIT}
 
 ERRORS = {
     -1: "BAD_ARG", -2: "SHAPE", -3: "DENOM", -4: "NONFINITE", -5: "WORKSPACE", -6: "CUDA",
@@ -141,8 +143,8 @@ def _stream_handle(stream) -> int:
 class Plan:
     """rimp2_plan for a fixed list of fragment shapes (nocc, nvir, naux)."""
 
-    def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 5,
-                 slices_t: int = 6, use_graph: bool = True, check_inputs: bool = True,
+    def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 0,
+                 slices_t: int = 0, use_graph: bool = True, check_inputs: bool = True,
                  max_workspace_bytes: int = 0, profile_stages: bool = False,
                  want_gamma: bool = True, want_p: bool = True, autotune: bool = False,
                  autotune_cache: str | None = None, stage_k: int = 0, n_tile: int = 0):

@@ -1,6 +1,6 @@
 """Full-size parity: the single large fragment (nocc=100, nvir=500, naux=1500, seed 0)
 in the configuration bench.py times (BF16 split, 5 slices for V, 6 for Gamma/P, CUDA
-graph), and the FP64 path.
+graph), the FP8 split mode (9 and 10 slices) and the FP64 path.
 
 The oracle cannot run the whole fragment in a test, so it computes sampled outputs one
 by one (pair energies, Gamma, P_ab and P_ij elements); identities that hold at any size
@@ -9,7 +9,9 @@ check the rest: E = sum_ij e_ij, <B, Gamma> = E (homogeneity), Tr P_ij = -Tr P_a
 
 Tolerances: split path vs oracle 1e-9 relative on sampled elements (pair energies
 1e-8 Eh absolute); split vs FP64 path total energy 1e-7 Eh (|E| ~ 1e7 Eh, ~1 ulp is
-2e-9); identities 1e-9 relative (split) and 1e-11 (FP64).
+2e-9); identities 1e-9 relative (split) and 1e-11 (FP64).  The total energy is the
+sharpest check of a one-signed error: the diagonal V_ii(a,a) carries a few per cent of
+E, so a bias of 2^-40 on it (an even V slice count under FP8) moves E by ~1e-6 Eh.
 """
 import numpy as np
 import pytest
@@ -27,7 +29,7 @@ DIMS = (100, 500, 1500)
 def c1():
     f = synth.fragment_inputs(*DIMS, seed=0)
     res = {}
-    for prec in ("bf16", "fp64"):
+    for prec in ("bf16", "fp8", "fp64"):
         eng = rimp2.Engine([DIMS], precision=prec)
         eng.set_inputs([f])
         eng.run()
@@ -59,16 +61,22 @@ def test_c1_identities_split(c1):
     _identities(f, r["bf16"], 1e-9)
 
 
+def test_c1_identities_fp8(c1):
+    f, r = c1
+    _identities(f, r["fp8"], 1e-9)
+
+
 def test_c1_identities_fp64(c1):
     f, r = c1
     _identities(f, r["fp64"], 1e-11)
 
 
-def test_c1_split_vs_fp64_energy(c1):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_c1_split_vs_fp64_energy(c1, prec):
     _, r = c1
-    assert abs(r["bf16"]["energy"] - r["fp64"]["energy"]) <= 1e-7
+    assert abs(r[prec]["energy"] - r["fp64"]["energy"]) <= 1e-7
     for k in ("gamma", "pij", "pab"):
-        a, b = r["bf16"][k], r["fp64"][k]
+        a, b = r[prec][k], r["fp64"][k]
         assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), k
 
 
@@ -76,7 +84,7 @@ def test_c1_sampled_outputs_vs_oracle(c1):
     f, r = c1
     rng = np.random.default_rng(42)
     nthr = oracle.threads()
-    for prec, tol in (("bf16", 1e-9), ("fp64", 1e-11)):
+    for prec, tol in (("bf16", 1e-9), ("fp8", 1e-9), ("fp64", 1e-11)):
         g = r[prec]
         for (i, j) in [(0, 0), (3, 77), (99, 12)]:
             ref = oracle.pair_energy(f.B, f.eo, f.ev, i, j, nthr)

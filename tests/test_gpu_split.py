@@ -34,12 +34,12 @@ def rel(a, b):
 def _hook():
     lib = rimp2.load()
     f = lib.rimp2_testing_slice_gemm_k
-    f.argtypes = [ctypes.c_int32] * 6 + [ctypes.c_void_p] * 4
+    f.argtypes = [ctypes.c_int32] * 7 + [ctypes.c_void_p] * 4
     f.restype = ctypes.c_int
     return f
 
 
-def _exact_levels(A, B, s, chunk=512):
+def _exact_levels(A, B, s, chunk=512, bits=8):
     """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the magnitude
     the kernel's rounding is relative to: sum over 512-long K chunks and levels of
     2^(-8 l) sum_k |A_p||B_q| (the usual dot-product error model)."""
@@ -55,8 +55,8 @@ def _exact_levels(A, B, s, chunk=512):
                 b = B[l - p, :, k0:k0 + chunk].astype(np.int64)
                 lev += a @ b.T
                 lab += np.abs(a) @ np.abs(b).T
-            out += lev.astype(np.float64) * 2.0 ** (-8 * l)
-            mag += lab.astype(np.float64) * 2.0 ** (-8 * l)
+            out += lev.astype(np.float64) * 2.0 ** (-bits * l)
+            mag += lab.astype(np.float64) * 2.0 ** (-bits * l)
     return out, mag
 
 
@@ -85,7 +85,7 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     Bd = torch.tensor(Bp, dtype=torch.bfloat16, device="cuda")
     assert torch.equal(Ad.float().cpu(), torch.tensor(Ap, dtype=torch.float32))
     C = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
-    rc = _hook()(M, N, K, kpad, s, stage_k, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+    rc = _hook()(M, N, K, kpad, s, stage_k, 0, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
                  torch.cuda.current_stream().cuda_stream)
     assert rc == 0
     ref, mag = _exact_levels(A, B, s)
@@ -93,6 +93,35 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     assert np.all(np.isfinite(got))
     # an FP32 accumulator alone would err by ~2^-24 of mag and one wrong integer in
     # levels 0..2 by >= 2^-16 (absolute); demand 2^-44 of the absolute products
+    bound = 2.0 ** -44 * (mag + 1.0)
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
+
+
+@pytest.mark.parametrize("M,N,K,s,seed", [
+    (128, 64, 64, 8, 0),         # worst case magnitudes, one stage
+    (200, 150, 1100, 8, 1),      # three chunks, ragged
+    (130, 48, 700, 10, 2),       # ten slices, 48-column tiles
+])
+def test_fp8_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
+    """FP8 e4m3 digits in [-16, 16], 5-bit levels: every level sum of a chunk is exact."""
+    rng = np.random.default_rng(seed)
+    kpad = (K + 15) // 16 * 16
+    A = rng.integers(-16, 17, size=(s, M, K))
+    B = rng.integers(-16, 17, size=(s, N, K))
+    if seed == 0:
+        A[:] = 16
+        B[:] = -16
+    Ap = np.zeros((s, M, kpad)); Ap[:, :, :K] = A
+    Bp = np.zeros((s, N, kpad)); Bp[:, :, :K] = B
+    Ad = torch.tensor(Ap, dtype=torch.float32).to(torch.float8_e4m3fn).cuda()
+    Bd = torch.tensor(Bp, dtype=torch.float32).to(torch.float8_e4m3fn).cuda()
+    assert torch.equal(Ad.float().cpu(), torch.tensor(Ap, dtype=torch.float32))
+    C = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
+    rc = _hook()(M, N, K, kpad, s, 64, 1, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+                 torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    ref, mag = _exact_levels(A, B, s, bits=5)
+    got = C.cpu().numpy()
     bound = 2.0 ** -44 * (mag + 1.0)
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
 
@@ -115,11 +144,14 @@ def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
     ((5, 31, 1), 5),
     ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
 ])
-@pytest.mark.parametrize("stage_k", [16, 32])
-def test_split_fragment_parity(dims, seed, stage_k):
+@pytest.mark.parametrize("mode", ["bf16-32", "bf16-16", "fp8"])
+def test_split_fragment_parity(dims, seed, mode):
     f = synth.fragment_inputs(*dims, seed=seed)
     ref = oracle.fragment(f.B, f.eo, f.ev)
-    out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=stage_k)
+    if mode == "fp8":
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8")
+    else:
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=int(mode[5:]))
     check_split(out, ref)
 
 
@@ -132,11 +164,12 @@ def test_split_degenerate_sizes():
             assert torch.count_nonzero(out[k]).item() == 0
 
 
-def test_split_uneven_batch_matches_oracle():
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_split_uneven_batch_matches_oracle(precision):
     s = synth.MonomerSystem(n_monomers=6, box=14.0, seed=0, nocc_range=(2, 5))
     polys = [(0,), (3,), (0, 1), (2, 4), (1, 3, 5), (0, 2, 4), (5,)]
     frags = [s.fragment(p) for p in polys]
-    eng = rimp2.Engine([f.B.shape for f in frags], precision="bf16")
+    eng = rimp2.Engine([f.B.shape for f in frags], precision=precision)
     eng.set_inputs(frags)
     eng.run()
     torch.cuda.synchronize()
