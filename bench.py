@@ -288,7 +288,7 @@ def main():
                 "peak_source": "measured DFMA peak (probes/dfma_peak.cu)"}
     else:
         fp8 = head == "fp8"
-        sv, stt = (9, args.slices_t or 10) if fp8 else (5, args.slices_t or 6)
+        sv, stt = (8, args.slices_t or 10) if fp8 else (5, args.slices_t or 6)
         prod_v, prod_t = sv * (sv + 1) // 2, stt * (stt + 1) // 2
         k = 3 if sm[3] >= sm[1] else 1
         Fk = F_c * prod_t if k == 3 else F_v * prod_v

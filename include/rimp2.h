@@ -97,11 +97,10 @@ typedef struct rimp2_batch {
 
 typedef struct rimp2_options {
   int32_t slices_v;    /* split modes: digit slices of B for V; 0 = default (BF16: 5
-                          slices of 8 bits, range 2..8; FP8: 9 slices of 5 bits, 2..10).
-                          The first even level the truncated product triangle drops
-                          holds the squared middle digit of the diagonal V_ii(a,a), a
-                          one-signed error of 2^(-bits x that level): an odd count
-                          keeps it one level further down */
+                          slices of 8 bits, range 2..8; FP8: 8 slices of 5 bits, 2..10).
+                          The diagonal V_ii(a,a) is taken from an FP64 row sum of
+                          squares: there both operands have the same digits and the
+                          truncated triangle's error would have one sign */
   int32_t slices_t;    /* split modes: slices for the Gamma/P operands; 0 = default
                           (BF16: 6, range 2..8; FP8: 10, range 2..10) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */

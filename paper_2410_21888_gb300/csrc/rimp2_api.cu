@@ -432,7 +432,7 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   rimp2_default_options(&o);
   if (opt) o = *opt;
   const bool fp8 = precision == RIMP2_FP8_SPLIT;
-  if (o.slices_v == 0) o.slices_v = fp8 ? 9 : 5;   // odd: see the header on slices_v
+  if (o.slices_v == 0) o.slices_v = fp8 ? 8 : 5;
   if (o.slices_t == 0) o.slices_t = fp8 ? 10 : 6;
   const int smax = fp8 ? 10 : 8;   // levels x tile width must fit the 512 TMEM columns
   if (precision != RIMP2_FP64 &&

@@ -484,7 +484,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             if (n >= P->N) continue;
             float s1, s2;
             pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB, s1, s2);
-            const df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
+            df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
+            if (n == m) {   // diagonal: the FP64 row sum of squares (see k_slice_b1)
+              const float2 w = ((const float2*)(wsb + P->vd_off))[m];
+              V = {w.x, w.y};
+            }
             const float2 dn = dv[n];
             const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
             const df T = df_div(V, D);

@@ -62,6 +62,7 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
   double alpha;
   long long d_off;            // PK_V: byte offset of float2 d_m = e_i - e_a per row
   long long et_off;           // PK_V: byte offset of the unsigned max-exponent slot of |T|
+  long long vd_off;           // PK_V: byte offset of float2 V_mm (diagonal, FP64 row sums)
   int v;                      // PK_V: nvir of the fragment
   int pad1;
 };

@@ -139,8 +139,12 @@ __global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases b
   sc[1] = 0;
 }
 
-// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, and the
-// fragment-wide maximum exponent used by the Gamma operand.
+// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, the diagonal
+// V_ii(a,a) = sum_Q (B^Q_ia)^2 in FP64 and the fragment-wide maximum exponent used by the
+// Gamma operand.  The diagonal is the one element of V whose two operands have the same
+// digits: there the truncated triangle's first dropped even level holds the square of
+// the middle digit, an error of one sign that does not average out; the epilogue takes
+// this FP64 value instead.
 template <bool F8>
 __global__ void __launch_bounds__(256)
 k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, Bases bs) {
@@ -151,10 +155,17 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
   const SplitFragDev& F = f[find_sfd(f, nf, gr, 0)];
   const int r = (int)(gr - F.row_begin);
   const double* x = bs.B + F.b_off + (long long)r * F.X;
-  double mx = 0.0;
-  for (int q = lane; q < F.X; q += 32) mx = fmax(mx, fabs(x[q]));
+  double mx = 0.0, ss = 0.0;
+  for (int q = lane; q < F.X; q += 32) {
+    const double xq = x[q];
+    mx = fmax(mx, fabs(xq));
+    ss = fma(xq, xq, ss);
+  }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  }
   const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
   char* ws = (char*)bs.ws;
   const long long plane = (long long)F.o * F.v * F.xpad;
@@ -165,6 +176,8 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
     const int i = r / F.v, a = r - i * F.v;
     const dfl d = d_from(bs.eps[F.eo_off + i] - bs.eps[F.ev_off + a]);
     ((float2*)(ws + F.drow))[r] = make_float2(d.h, d.l);
+    const dfl vd = d_from(ss);
+    ((float2*)(ws + F.vdrow))[r] = make_float2(vd.h, vd.l);
     if (mx > 0.0) atomicMax((int*)(ws + F.scal), E);
   }
 }
@@ -380,7 +393,7 @@ void split_plan_release(SplitPlan&) {}
 namespace {
 
 struct Layout {
-  size_t bs1, bs2, erow, drow, thi, tlo, tts, ts, ep, scal, total;
+  size_t bs1, bs2, erow, drow, vdrow, thi, tlo, tts, ts, ep, scal, total;
 };
 
 // element size of the digit planes and the padding that keeps every row 16-byte aligned
@@ -401,6 +414,7 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   L.bs2 = off; off += al256(st_g * X * RL * esz);
   L.erow = off; off += al256(ov * 4);
   L.drow = off; off += al256(ov * 8);
+  L.vdrow = off; off += al256(ov * 8);
   L.thi = off; off += al256(ov * ov * 4);
   L.tlo = off; off += al256(ov * ov * 4);
   L.tts = off; off += al256(st_t * ov * RL * esz);
@@ -462,6 +476,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
     s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
     s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
+    s.vdrow = off + L.vdrow;
     s.thi = off + L.thi; s.tlo = off + L.tlo; s.tts = off + L.tts; s.ts = off + L.ts;
     s.ep = off + L.ep; s.scal = off + L.scal;
     s.pair_begin = pairs; s.row_begin = rows; s.b2_tile_begin = b2t;
@@ -496,7 +511,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
       P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ov; P.alpha = 1.0;
-      P.d_off = s.drow; P.et_off = s.scal + 4; P.v = v;
+      P.d_off = s.drow; P.vd_off = s.vdrow; P.et_off = s.scal + 4; P.v = v;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
       const uint64_t str[2] = {(uint64_t)xpad * E2, (uint64_t)ov * xpad * E2};

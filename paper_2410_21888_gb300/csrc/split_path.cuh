@@ -18,6 +18,7 @@ struct SplitFragDev {
   long long bs2;    // B digits for Gamma: [s_t][X][o*vpad] bf16, one scale
   long long erow;   // int32 [o*v] row exponents of bs1
   long long drow;   // float2 [o*v]: e_i - e_a as a double-float
+  long long vdrow;  // float2 [o*v]: V_ii(a,a) = sum_Q (B^Q_ia)^2 (FP64 sum) as a double-float
   long long thi, tlo;  // float [o*v][o*v]: T as a double-float pair of planes
   long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
   long long ep;     // double [o][o] pair energies

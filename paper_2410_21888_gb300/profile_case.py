@@ -21,10 +21,10 @@ def main():
     ap.add_argument("--nocc", type=int, default=24)
     ap.add_argument("--nvir", type=int, default=200)
     ap.add_argument("--naux", type=int, default=600)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp64"])
     ap.add_argument("--calls", type=int, default=1)
-    ap.add_argument("--slices-v", type=int, default=5)
-    ap.add_argument("--slices-t", type=int, default=6)
+    ap.add_argument("--slices-v", type=int, default=0, help="0: the library default")
+    ap.add_argument("--slices-t", type=int, default=0, help="0: the library default")
     a = ap.parse_args()
     f = synth.fragment_inputs(a.nocc, a.nvir, a.naux, seed=0)
     eng = rimp2.Engine([f.B.shape], precision=a.precision, slices_v=a.slices_v,

@@ -1,6 +1,6 @@
 """Full-size parity: the single large fragment (nocc=100, nvir=500, naux=1500, seed 0)
 in the configuration bench.py times (BF16 split, 5 slices for V, 6 for Gamma/P, CUDA
-graph), the FP8 split mode (9 and 10 slices) and the FP64 path.
+graph), the FP8 split mode (8 and 10 slices) and the FP64 path.
 
 The oracle cannot run the whole fragment in a test, so it computes sampled outputs one
 by one (pair energies, Gamma, P_ab and P_ij elements); identities that hold at any size
@@ -11,7 +11,7 @@ Tolerances: split path vs oracle 1e-9 relative on sampled elements (pair energie
 1e-8 Eh absolute); split vs FP64 path total energy 1e-7 Eh (|E| ~ 1e7 Eh, ~1 ulp is
 2e-9); identities 1e-9 relative (split) and 1e-11 (FP64).  The total energy is the
 sharpest check of a one-signed error: the diagonal V_ii(a,a) carries a few per cent of
-E, so a bias of 2^-40 on it (an even V slice count under FP8) moves E by ~1e-6 Eh.
+E, so a relative bias of 2^-40 on it moves E by ~1e-6 Eh.
 """
 import numpy as np
 import pytest

@@ -186,3 +186,18 @@ def test_split_error_decreases_with_slices():
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", slices_v=s, slices_t=s)
         errs.append(rel(out["gamma"].cpu().numpy(), ref["gamma"]))
     assert errs[0] > errs[1] > errs[2] or errs[2] < 1e-12, errs
+
+
+@pytest.mark.parametrize("dims", [(4, 60, 4000), (8, 40, 2000)])
+@pytest.mark.parametrize("precision,sv,tol", [("bf16", 4, 2e-11), ("fp8", 8, 1e-12)])
+def test_diagonal_dominated_energy_has_no_one_signed_error(dims, precision, sv, tol):
+    """With naux >> nocc*nvir most of E comes from the diagonal V_ii(a,a) = sum_Q B^2,
+    whose two operands have identical digits.  Were it taken from the truncated product
+    triangle, the squared middle digit of the first dropped even level (BF16 4 slices:
+    level 4, 2^-32; FP8 8 slices: level 8, 2^-40) would shift E by ~2e-9 and ~1e-11
+    relative; from the FP64 row sum it stays at the random truncation level."""
+    f = synth.fragment_inputs(*dims, seed=5)
+    ref = oracle.fragment(f.B, f.eo, f.ev, want=())["energy"]
+    out = rimp2.energy_grad(f.B, f.eo, f.ev, precision=precision, slices_v=sv,
+                            want_gamma=False, want_p=False)
+    assert abs(float(out["energy"].item()) - ref) <= tol * abs(ref)
