@@ -32,7 +32,11 @@ DIMS = (100, 500, 1500)
 FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)
 # dram read+write bytes per launch of the dominant kernel from an ncu capture (None until
 # measured for the current kernel); keyed by stage index
-TRAFFIC_PER_LAUNCH = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the contraction kernel on the
+# nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture (profiles/split_gemm_c1_dram.md);
+# keyed by (precision, stage): 1 = V, 3 = Gamma/P.  Cleared whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {("bf16", 3): 845_084_850_176 + 618_203_136,
+                      ("bf16", 1): 151_775_866_368 + 21_264_399_872}
 
 
 def flops(o, v, X):
@@ -296,7 +300,7 @@ def main():
         # FP8 dense peak: the measured BF16 peak x the nominal FP8:BF16 ratio (4.5 / 2.25)
         peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if fp8 else 1.0)
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get(k),
+                "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get((head, k)),
                 "kernel": "k_split_gemm (" + (f"Gamma/P_ab/P_ij, {prod_t} slice products"
                                               if k == 3 else f"V, {prod_v} slice products") + ")",
                 "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)"
