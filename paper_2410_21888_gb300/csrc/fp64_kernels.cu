@@ -324,16 +324,19 @@ cudaError_t launch_energy_reduce(const FragDev* d_frags, int nfrag, Bases bs, cu
 __global__ void k_zero_p(const FragDev* __restrict__ frags, Bases bs) {
   const FragDev F = frags[blockIdx.y];
   const long long no = (long long)F.o * F.o, nv = (long long)F.v * F.v;
+  const long long ng = (F.zero_gamma && F.gamma_off >= 0) ? (long long)F.o * F.v * F.X : 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < no + nv; e += stride) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < no + nv + ng;
+       e += stride) {
     if (e < no) { if (F.pij_off >= 0) bs.pij[F.pij_off + e] = 0.0; }
-    else if (F.pab_off >= 0) bs.pab[F.pab_off + (e - no)] = 0.0;
+    else if (e < no + nv) { if (F.pab_off >= 0) bs.pab[F.pab_off + (e - no)] = 0.0; }
+    else bs.gamma[F.gamma_off + (e - no - nv)] = 0.0;
   }
 }
 
 cudaError_t launch_zero_p(const FragDev* d_frags, int nfrag, Bases bs, cudaStream_t s) {
   if (nfrag <= 0) return cudaSuccess;
-  k_zero_p<<<dim3(64, nfrag), 256, 0, s>>>(d_frags, bs);
+  k_zero_p<<<dim3(256, nfrag), 256, 0, s>>>(d_frags, bs);
   return cudaGetLastError();
 }
 

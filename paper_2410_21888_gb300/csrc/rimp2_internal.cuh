@@ -56,6 +56,7 @@ struct GemmProb {
 // Per-fragment info used by the elementwise / reduction kernels.
 struct FragDev {
   int o, v, X, idx;           // idx: position in the batch (energy[idx])
+  int zero_gamma, pad0;       // 1: Gamma is accumulated by atomics, zero it first
   long long b_off, eo_off, ev_off;
   long long t_off, tt_off, ep_off;   // workspace offsets (elements)
   long long gamma_off, pij_off, pab_off, epair_off;  // -1: not requested

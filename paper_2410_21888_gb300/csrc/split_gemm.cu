@@ -160,6 +160,38 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          ((uint64_t)1u << 46) | (layout << 61);
 }
 
+// All MMAs of one pipeline stage for S slices, unrolled: for each K step of 16 (BF16) or
+// 32 (FP8) elements and each A slice p, one MMA against the contiguous B slices
+// q0 .. q0+nq-1 (nq * NT <= 256 columns) writes the column block of B_q into the level-(p+q)
+// accumulator at TMEM column (p+q) * NT.  `desc` is the shared-memory descriptor of the
+// stage base; every operand tile starts a constant number of 16-byte units above it and
+// shared addresses stay below 256 KB, so the 14-bit start field never carries.  The first
+// stage of a TMEM chunk (fresh) overwrites the accumulators through the p = 0 MMAs.
+template <int S, int NT, int ROWB, bool F8>
+__device__ __forceinline__ void mma_stage(uint32_t tmem_base, uint64_t desc, uint32_t idesc_m,
+                                          bool fresh) {
+  if constexpr (S * NT <= 512) {
+    constexpr int kGroup = 256 / NT;
+    constexpr uint32_t A16 = (SG_BM * ROWB) >> 4, B16 = (NT * ROWB) >> 4;
+#pragma unroll
+    for (int k16 = 0; k16 < ROWB / 32; ++k16) {
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
+#pragma unroll
+        for (int q0 = 0; q0 + p < S; q0 += kGroup) {
+          const int nq = kGroup < S - p - q0 ? kGroup : S - p - q0;
+          const uint64_t adesc = desc + (uint64_t)(p * A16 + k16 * 2);
+          const uint64_t bdesc = desc + (uint64_t)(S * A16 + q0 * B16 + k16 * 2);
+          const uint32_t idesc = idesc_m | ((uint32_t)((nq * NT) >> 3) << 17);
+          const uint32_t acc = (fresh && k16 == 0 && p == 0) ? 0u : 1u;
+          if (F8) umma_f8(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
+          else umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ double-float
 
 struct df { float h, l; };
@@ -217,11 +249,27 @@ __device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ pr
   }
   TileInfo ti;
   ti.P = probs + lo;
-  const long long lt = t - ti.P->tile_begin;
-  const int ks = (int)(lt % ti.P->ksplit);
-  const long long tt = lt / ti.P->ksplit;
-  ti.tm = (int)(tt / ti.P->tiles_n);
-  ti.tn = (int)(tt % ti.P->tiles_n);
+  const SplitProb* P = ti.P;
+  const long long lt = t - P->tile_begin;
+  const long long per = (long long)P->tiles_m * P->tiles_n;
+  int ks;
+  long long tt;
+  if (P->ks_outer) { ks = (int)(lt / per); tt = lt - (long long)ks * per; }
+  else { ks = (int)(lt % P->ksplit); tt = lt / P->ksplit; }
+  if (P->group_m > 1) {
+    // groups of group_m rows, walked column by column: the group's A rows stay in L2
+    // while each column block of B is used by group_m tiles that run side by side
+    const long long gsz = (long long)P->group_m * P->tiles_n;
+    const int g = (int)(tt / gsz);
+    const int first = g * P->group_m;
+    const int gm = min(P->group_m, P->tiles_m - first);
+    const int r = (int)(tt - g * gsz);
+    ti.tm = first + r % gm;
+    ti.tn = r / gm;
+  } else {
+    ti.tm = (int)(tt / P->tiles_n);
+    ti.tn = (int)(tt % P->tiles_n);
+  }
   ti.k1b = ks * ti.P->k1_chunk;
   ti.k1e = min(ti.P->k1_count, ti.k1b + ti.P->k1_chunk);
   ti.nK = max(0, ti.k1e - ti.k1b) * ti.P->k0_blocks;
@@ -235,6 +283,7 @@ __device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ pr
 __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
                                             int mode, int x, int row, int k1, int div5, int slice) {
   if (mode == TM_3D) tma_3d(dst, tm, bar, x, row, slice);
+  else if (mode == TM_3DK) tma_3d(dst, tm, bar, k1 * div5 + x, row, slice);
   else if (mode == TM_4D) tma_4d(dst, tm, bar, x, row, k1, slice);
   else tma_5d(dst, tm, bar, x, k1 / div5, k1 % div5, row, slice);
 }
@@ -352,7 +401,6 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       // K-major, M = 128; N (a multiple of NT up to 256) is or-ed in per MMA
       constexpr uint32_t kFmt = F8 ? 0u : 1u;   // E4M3 (kind::f8f6f4) or BF16 (kind::f16)
       const uint32_t idesc_m = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(SG_BM >> 4) << 24);
-      constexpr int kGroup = 256 / NT;
       uint32_t st = 0, ph = 0, te_count = 0;
       int tslot = 0;
       uint32_t tph = 0;
@@ -374,23 +422,19 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           for (int kk = c * CHUNK_STAGES; kk < kend; ++kk) {
             if (!mbar_wait(full + st, ph, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
-#pragma unroll
-            for (int k16 = 0; k16 < ROWB / 32; ++k16) {
-              for (int p = 0; p < slices; ++p) {
-                const uint64_t adesc = smem_desc<ROWB>(base + p * A_TILE) + (uint64_t)(k16 * 2);
-                // one MMA of A_p against the contiguous B tiles q0 .. q0+nq-1: the column
-                // block of B_q lands on the level-(p+q) accumulator at (p+q) * NT
-                for (int q0 = 0; q0 + p < slices; q0 += kGroup) {
-                  const int nq = min(kGroup, slices - p - q0);
-                  const uint64_t bdesc =
-                      smem_desc<ROWB>(base + slices * A_TILE + q0 * B_TILE) + (uint64_t)(k16 * 2);
-                  const uint32_t acc = (kk == c * CHUNK_STAGES && k16 == 0 && p == 0) ? 0u : 1u;
-                  const uint32_t idesc = idesc_m | ((uint32_t)((nq * NT) >> 3) << 17);
-                  if (F8) umma_f8(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
-                  else umma_bf16(tmem_base + (uint32_t)((p + q0) * NT), adesc, bdesc, idesc, acc);
-                }
-              }
+            const uint64_t desc = smem_desc<ROWB>(smem_u32(smem + (size_t)st * stage_bytes));
+            const bool fresh = kk == c * CHUNK_STAGES;
+            switch (slices) {
+              case 2: mma_stage<2, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 3: mma_stage<3, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 4: mma_stage<4, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 5: mma_stage<5, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 6: mma_stage<6, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 7: mma_stage<7, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 8: mma_stage<8, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 9: mma_stage<9, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 10: mma_stage<10, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              default: break;   // rejected by the host (slices in 2..10, slices * NT <= 512)
             }
             umma_commit(empty + st);   // frees this smem stage once its MMAs completed
             if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
@@ -478,6 +522,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           float* Tl = (float*)(wsb + P->c2_off);
           const float2* dv = (const float2*)(wsb + P->d_off);
           const float2 dm = dv[m];
+          const int im = m / P->v;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const int n = nbase + c;
@@ -492,10 +537,17 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             const float2 dn = dv[n];
             const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
             const df T = df_div(V, D);
-            Th[(long long)m * P->ldc + n] = T.h;
-            Tl[(long long)m * P->ldc + n] = T.l;
-            Th[(long long)n * P->ldc + m] = T.h;
-            Tl[(long long)n * P->ldc + m] = T.l;
+            // the amplitude stage reads the pair blocks i <= j only: store (m, n) where
+            // i(m) <= i(n) and the mirror (n, m) where i(n) <= i(m)
+            const int jn = n / P->v;
+            if (im <= jn) {
+              Th[(long long)m * P->ldc + n] = T.h;
+              Tl[(long long)m * P->ldc + n] = T.l;
+            }
+            if (jn <= im) {
+              Th[(long long)n * P->ldc + m] = T.h;
+              Tl[(long long)n * P->ldc + m] = T.l;
+            }
             emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
           }
         } else {

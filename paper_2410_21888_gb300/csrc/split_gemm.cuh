@@ -37,6 +37,7 @@ enum : int {
   TM_3D = 0,    // {k0*32, row, slice}
   TM_4D = 1,    // {k0*32, row, k1, slice}
   TM_5D = 2,    // {k0*32, k1 / div, k1 % div, row, slice}
+  TM_3DK = 3,   // {k1*div + k0*32, row, slice}: a flat K cut into slabs of div elements
 };
 
 // Extra problem kind used only by the testing hook: store sum_l 2^-8l S_l * 2^(EA+EB-16)
@@ -53,7 +54,7 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
   int a_mode, b_mode, div5;
   int ea_rows, eb_rows;   // 1: per-row int32 exponent array; 0: one int32 scalar
   int ea_add, eb_add;     // added to the stored exponent
-  int pad0;
+  int ks_outer;           // 1: the split (slab) index is the slowest index of the tile order
   long long tile_begin, ntiles;
   long long ea_off, eb_off;   // byte offsets into the workspace (int32 data)
   long long c_off, c2_off;    // outputs: PK_V: byte offsets of T_hi / T_lo planes in ws;
@@ -64,7 +65,7 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
   long long et_off;           // PK_V: byte offset of the unsigned max-exponent slot of |T|
   long long vd_off;           // PK_V: byte offset of float2 V_mm (diagonal, FP64 row sums)
   int v;                      // PK_V: nvir of the fragment
-  int pad1;
+  int group_m;                // > 1: tiles walked in groups of group_m rows, column by column
 };
 
 struct SplitLaunch {

@@ -26,6 +26,11 @@ namespace rimp2 {
 namespace {
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// V tiles are walked in groups of this many rows (tile order, see decode_tile)
+constexpr int kVGroupRows = 16;
+// K extent of one Gamma slab (elements of the contracted (j,b) index)
+constexpr long long kGammaSlabK = 2048;
 int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
@@ -512,6 +517,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
       P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ov; P.alpha = 1.0;
       P.d_off = s.drow; P.vd_off = s.vdrow; P.et_off = s.scal + 4; P.v = v;
+      P.group_m = kVGroupRows;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
       const uint64_t str[2] = {(uint64_t)xpad * E2, (uint64_t)ov * xpad * E2};
@@ -529,10 +535,22 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTt - 1) / NTt;
       P.ksplit = 1; P.k0_blocks = (RL + BKt - 1) / BKt; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
+      // K = (j,b) cut into slabs of about kGammaSlabK elements, slab index outermost: the
+      // tiles in flight then share one slab, whose B digits stay in L2, and the tiles of a
+      // row start close enough together to share their Tt rows there too
+      const int kb = P.k0_blocks;
+      int slabs = sp.variant == 3 ? 1 : (int)(((long long)kb * BKt + kGammaSlabK / 2) / kGammaSlabK);
+      if (slabs > 1) {
+        const int per = (kb + slabs - 1) / slabs;
+        slabs = (kb + per - 1) / per;
+        P.k0_blocks = per; P.k1_count = slabs; P.ksplit = slabs;
+        P.a_mode = P.b_mode = TM_3DK; P.div5 = per * BKt; P.ks_outer = 1;
+        fdev.back().zero_gamma = 1;
+      }
       P.ea_rows = P.eb_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
       P.eb_off = s.scal; P.eb_add = 0;
       P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
-      P.ntiles = (long long)P.tiles_m * P.tiles_n;
+      P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)st};
       const uint64_t sA[2] = {(uint64_t)RL * E2, plane_b};
       const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};

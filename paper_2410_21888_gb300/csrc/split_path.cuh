@@ -40,7 +40,9 @@ struct SplitPlan {
 //   0: P_ij rows read through the local (k,b)-major view, split-K target 2 x grid
 //   1: P_ij rows read through the direct (i,a)-major view, split-K target 2 x grid
 //   2: local view, split-K target 4 x grid
-constexpr int kSplitVariants = 3;
+//   3: as 0, with Gamma's K in one piece (no slabs, no atomics on Gamma)
+// Variants 0..2 cut Gamma's K into slabs accumulated with FP64 atomics.
+constexpr int kSplitVariants = 4;
 
 struct SplitWave {
   std::vector<SplitFragDev> sfd;

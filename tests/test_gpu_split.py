@@ -143,6 +143,7 @@ def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
     ((1, 1, 1), 1),
     ((5, 31, 1), 5),
     ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
+    ((13, 333, 150), 8),     # Gamma's K (j,b) in two slabs, the last block past the end
 ])
 @pytest.mark.parametrize("mode", ["bf16-32", "bf16-16", "fp8"])
 def test_split_fragment_parity(dims, seed, mode):
