@@ -35,8 +35,7 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the contraction kernel on the
 # nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture (profiles/split_gemm_c1_dram.md);
 # keyed by (precision, stage): 1 = V, 3 = Gamma/P.  Cleared whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {("bf16", 3): 845_084_850_176 + 618_203_136,
-                      ("bf16", 1): 151_775_866_368 + 21_264_399_872}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def flops(o, v, X):
