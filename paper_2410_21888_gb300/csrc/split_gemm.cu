@@ -541,12 +541,14 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             // i(m) <= i(n) and the mirror (n, m) where i(n) <= i(m)
             const int jn = n / P->v;
             if (im <= jn) {
-              Th[(long long)m * P->ldc + n] = T.h;
-              Tl[(long long)m * P->ldc + n] = T.l;
+              const long long ix = (long long)m * P->ldc + n + (long long)jn * (P->vpad - P->v);
+              Th[ix] = T.h;
+              Tl[ix] = T.l;
             }
             if (jn <= im) {
-              Th[(long long)n * P->ldc + m] = T.h;
-              Tl[(long long)n * P->ldc + m] = T.l;
+              const long long ix = (long long)n * P->ldc + m + (long long)im * (P->vpad - P->v);
+              Th[ix] = T.h;
+              Tl[ix] = T.l;
             }
             emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
           }

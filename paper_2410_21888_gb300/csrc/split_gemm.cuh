@@ -66,6 +66,8 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
   long long vd_off;           // PK_V: byte offset of float2 V_mm (diagonal, FP64 row sums)
   int v;                      // PK_V: nvir of the fragment
   int group_m;                // > 1: tiles walked in groups of group_m rows, column by column
+  int vpad;                   // PK_V: T plane column of (j,b) is j*vpad + b
+  int pad2;
 };
 
 struct SplitLaunch {

@@ -77,14 +77,6 @@ __device__ __forceinline__ int find_sfd(const SplitFragDev* __restrict__ f, int 
   return lo;
 }
 
-__device__ __forceinline__ void tri_rc(long long t, int& r, int& c) {
-  long long cc = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while (cc * (cc + 1) / 2 > t) --cc;
-  while ((cc + 1) * (cc + 2) / 2 <= t) ++cc;
-  c = (int)cc;
-  r = (int)(t - cc * (cc + 1) / 2);
-}
-
 // One digit (an integer in [-2^(LB-1), 2^(LB-1)]) in the slice format: BF16 (LB = 8)
 // or FP8 e4m3 (LB = 5); both represent these integers exactly.
 template <bool F8> struct Digit;
@@ -112,25 +104,6 @@ __device__ __forceinline__ void digits_f64(double x, int E, int s, typename Digi
     const double d = rint(X);
     out[p * plane] = Digit<F8>::enc((float)d);
     X = (X - d) * (double)(1 << LB);
-  }
-}
-
-// Same for a double-float (h, l): d_p = rint(X_h); the remainder (X_h - d_p) is exact and
-// is re-joined with X_l by an error-free sum before the next scaling by 2^LB.
-template <bool F8>
-__device__ __forceinline__ void digits_df(dfl x, int E, int s, typename Digit<F8>::T* out,
-                                          long long plane) {
-  constexpr int LB = Digit<F8>::LB;
-  const int e = max(-252, min(254, LB - E));
-  const int e1 = e / 2, e2 = e - e1;
-  const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-  float xh = (x.h * s1) * s2, xl = (x.l * s1) * s2;
-  for (int p = 0; p < s; ++p) {
-    const float d = rintf(xh);
-    out[p * plane] = Digit<F8>::enc(d);
-    const dfl r = d_two_sum(xh - d, xl);
-    xh = r.h * (float)(1 << LB);
-    xl = r.l * (float)(1 << LB);
   }
 }
 
@@ -214,149 +187,197 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   __syncthreads();
   char* ws = (char*)bs.ws;
   const int E = *(const int*)(ws + F.scal);
-  const long long plane = (long long)F.X * RL;
+  const long long plane = (long long)F.X * F.ldd;
   DT* out = (DT*)(ws + F.bs2);
   for (int r = ty; r < 32; r += 8) {
     const int Q = tq * 32 + r, c = tc * 32 + tx;
-    if (Q < F.X && c < RL) digits_f64<F8>(tile[tx][r], E, st, out + (long long)Q * RL + c, plane);
+    if (Q < F.X && c < RL) digits_f64<F8>(tile[tx][r], E, st, out + (long long)Q * F.ldd + c, plane);
   }
 }
 
-// One CTA per pair block (i <= j): reads T_ij from the double-float planes, writes the
-// digits of Tt and T for the (i,j) block and, if i != j, the (j,i) block, zeroes the
-// row padding, and stores the pair energy e_ij = sum_ab Tt_ij(a,b) T_ij(a,b) D_ijab.
+// Four digits of one slice, packed for one store: BF16 digits are exact integers, so their
+// bit patterns are the upper halves of the FP32 values; FP8 digits go through the e4m3
+// conversion.
+template <bool F8> struct Pack4;
+template <> struct Pack4<false> {
+  using T = uint2;
+  __device__ static T pack(float d0, float d1, float d2, float d3) {
+    return make_uint2(__byte_perm(__float_as_uint(d0), __float_as_uint(d1), 0x7632),
+                      __byte_perm(__float_as_uint(d2), __float_as_uint(d3), 0x7632));
+  }
+};
+template <> struct Pack4<true> {
+  using T = uint32_t;
+  __device__ static T pack(float d0, float d1, float d2, float d3) {
+    return (uint32_t)Digit<true>::enc(d0) | ((uint32_t)Digit<true>::enc(d1) << 8) |
+           ((uint32_t)Digit<true>::enc(d2) << 16) | ((uint32_t)Digit<true>::enc(d3) << 24);
+  }
+};
+
+// One digit step of a normalised double-float (|xl| <= ulp(xh)/2) relative to the current
+// scale: d = rint(xh) by the 1.5 * 2^23 shift (round to nearest even, |xh| <= 2^22);
+// xh - d is exact and, when non-zero, a multiple of ulp(xh) >= 2|xl|, so Fast2Sum re-joins
+// it with xl exactly; the remainder is scaled by 2^LB for the next digit.
+template <int LB>
+__device__ __forceinline__ float digit_step(float& xh, float& xl) {
+  const float kShift = 12582912.f;
+  const float d = __fsub_rn(__fadd_rn(xh, kShift), kShift);
+  const float a = __fsub_rn(xh, d);
+  const float s = __fadd_rn(a, xl);
+  const float e = __fsub_rn(xl, __fsub_rn(s, a));
+  xh = s * (float)(1 << LB);
+  xl = e * (float)(1 << LB);
+  return d;
+}
+
+// Digits of four consecutive elements (double-floats x[k] already scaled to the slice
+// frame), one packed store per slice plane.
 template <bool F8>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* out,
+                                     long long plane) {
+  constexpr int LB = Digit<F8>::LB;
+  using PT = typename Pack4<F8>::T;
+  for (int p = 0; p < st; ++p) {
+    const float d0 = digit_step<LB>(x[0].h, x[0].l);
+    const float d1 = digit_step<LB>(x[1].h, x[1].l);
+    const float d2 = digit_step<LB>(x[2].h, x[2].l);
+    const float d3 = digit_step<LB>(x[3].h, x[3].l);
+    *(PT*)(out + p * plane) = Pack4<F8>::pack(d0, d1, d2, d3);
+  }
+}
+
+// One CTA per ordered pair (i, j), i-major, so that the CTAs in flight fill the same rows
+// of the digit planes.  The CTA writes the (i,j) block only; it reads the stored block
+// (min(i,j), max(i,j)) of the double-float T planes (rows (i,a), columns j*vpad + b;
+// T_ij(a,b) = T_ji(b,a)) in pairs of 32 x 32 tiles (ta <= tb): X = tile (ta, tb) and
+// Y = tile (tb, ta), 16-byte loads prefetched into registers while the previous pair is
+// processed.  Every thread forms, for one row and four consecutive columns of the output
+// tiles (ta, tb) and (tb, ta), Tt = 2T - T^T and the digits of T and Tt (one packed store
+// per slice; columns in [nvir, vpad) get zero digits).  CTAs with i <= j also accumulate
+// the pair energy e_ij = sum_ab Tt_ij(a,b) T_ij(a,b) D_ijab in double-float (D from the
+// double-float row terms d_m = e_i - e_a).
+template <bool F8>
+__global__ void __launch_bounds__(256, 3)
 k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   using DT = typename Digit<F8>::T;
-  __shared__ float Xh[32][33], Xl[32][33], Yh[32][33], Yl[32][33];
-  // per tile pair: r_a = (e_i + e_j) - e_a for rows and e_b for columns, as double-floats
-  // (formed once per row/column in FP64, so the inner loops stay in FP32)
-  __shared__ float Rta[2][32], Rtb[2][32], Eta[2][32], Etb[2][32];
-  __shared__ double red_h[8], red_l[8];
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  constexpr int LB = Digit<F8>::LB;
+  __shared__ float2 Xs[32][33], Ys[32][33];
+  __shared__ float red_h[8], red_l[8];
+  const int tid = threadIdx.x, r = tid >> 3, c0 = (tid & 7) * 4;
   const long long gp = blockIdx.x;
   const SplitFragDev& F = f[find_sfd(f, nf, gp, 2)];
-  int i, j;
-  tri_rc(gp - F.pair_begin, i, j);
-  const int v = F.v, o = F.o;
-  const long long ov = (long long)o * v;
-  const int RL = o * F.vpad;
+  const int v = F.v, o = F.o, vpad = F.vpad;
+  const int i = (int)((gp - F.pair_begin) / o), j = (int)((gp - F.pair_begin) % o);
+  const bool tr = i > j;                  // the stored block is (j, i)
+  const int i0 = tr ? j : i, j0 = tr ? i : j;
+  const long long ldd = F.ldd, ldt = F.ldt;
   st = F.st_out;           // 0: energy only, no digit planes for this fragment
   char* ws = (char*)bs.ws;
   const float* Th = (const float*)(ws + F.thi);
   const float* Tl = (const float*)(ws + F.tlo);
+  const float2* dr = (const float2*)(ws + F.drow);
   const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
-  const int E_T = (int)emax - 124, E_Tt = (int)emax - 123;
+  float s1t, s2t, s1tt, s2tt;   // 2^(LB - E) as two normal factors, for T and Tt
+  {
+    const int et = max(-252, min(254, LB - ((int)emax - 124)));
+    const int ett = max(-252, min(254, LB - ((int)emax - 123)));
+    s1t = __int_as_float(((et / 2) + 127) << 23);
+    s2t = __int_as_float(((et - et / 2) + 127) << 23);
+    s1tt = __int_as_float(((ett / 2) + 127) << 23);
+    s2tt = __int_as_float(((ett - ett / 2) + 127) << 23);
+  }
   DT* tts = (DT*)(ws + F.tts);
   DT* ts = (DT*)(ws + F.ts);
-  const long long plane = ov * RL;
-  const double* eo = bs.eps + F.eo_off;
-  const double* ev = bs.eps + F.ev_off;
-  const double eij = eo[i] + eo[j];
-  const long long rowI = (long long)i * v, rowJ = (long long)j * v;
-  const int colI = i * F.vpad, colJ = j * F.vpad;
-  dfl e_acc = {0.f, 0.f};
+  const long long plane = (long long)o * v * ldd;
+  const long long rowI = (long long)i * v, rowJ = (long long)j * v;      // output rows, D terms
+  const long long colJ = (long long)j * vpad;                            // output columns
+  const long long rowS = (long long)i0 * v, colS = (long long)j0 * vpad; // stored block
   const int nt = (v + 31) / 32;
-  const long long npairs = (long long)nt * (nt + 1) / 2;
+  dfl e_acc = {0.f, 0.f};
 
-  auto put = [&](long long row, int col, dfl t, dfl tt) {
-    const long long o_ = row * RL + col;
-    digits_df<F8>(t, E_T, st, ts + o_, plane);
-    digits_df<F8>(tt, E_Tt, st, tts + o_, plane);
+  float4 xh, xl, yh, yl;
+  auto load = [&](int ta, int tb) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    xh = xl = yh = yl = z;
+    const int ax = ta * 32 + r, bx = tb * 32 + c0;
+    if (ax < v && bx < vpad) {
+      const long long ix = (rowS + ax) * ldt + colS + bx;
+      xh = __ldg((const float4*)(Th + ix));
+      xl = __ldg((const float4*)(Tl + ix));
+    }
+    const int ay = tb * 32 + r, by = ta * 32 + c0;
+    if (ay < v && by < vpad) {
+      const long long iy = (rowS + ay) * ldt + colS + by;
+      yh = __ldg((const float4*)(Th + iy));
+      yl = __ldg((const float4*)(Tl + iy));
+    }
   };
 
-  for (long long q = 0; q < npairs; ++q) {
-    int ta, tb;
-    tri_rc(q, ta, tb);
+  // one output tile row segment: t_k and its transposed partner y_k for the four columns
+  // col0 + k (local column index lc0 + k of the output block), written at global row orow
+  auto emit = [&](const dfl t_in[4], const dfl y_in[4], long long orow, long long ocol0, int lc0,
+                  bool energy, long long drow_r, long long drow_c0) {
+    dfl t[4], tt[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int l = ty + 8 * r;
-      const int a = ta * 32 + l, b = tb * 32 + tx;
-      const bool okx = a < v && b < v;
-      const long long ix = (rowI + a) * ov + rowJ + b;
-      Xh[l][tx] = okx ? Th[ix] : 0.f;
-      Xl[l][tx] = okx ? Tl[ix] : 0.f;
-      const int a2 = tb * 32 + l, b2 = ta * 32 + tx;
-      const bool oky = a2 < v && b2 < v;
-      const long long iy = (rowI + a2) * ov + rowJ + b2;
-      Yh[l][tx] = oky ? Th[iy] : 0.f;
-      Yl[l][tx] = oky ? Tl[iy] : 0.f;
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = lc0 + k < v;
+      t[k] = ok ? t_in[k] : dfl{0.f, 0.f};
+      tt[k] = ok ? d_add({2.f * t_in[k].h, 2.f * t_in[k].l}, d_neg(y_in[k])) : dfl{0.f, 0.f};
+      if (energy && ok) {
+        const float2 dm = dr[drow_r], dn = dr[drow_c0 + k];
+        const dfl D = d_add({dm.x, dm.y}, {dn.x, dn.y});
+        e_acc = d_add(e_acc, d_mul(tt[k], d_mul(t[k], D)));
+      }
     }
-    if (ty < 2) {
-      const int t = ty == 0 ? ta : tb;
-      const int k = t * 32 + tx;
-      const dfl r = d_from(k < v ? eij - ev[k] : 0.0);
-      const dfl e = d_from(k < v ? ev[k] : 0.0);
-      float (*R)[32] = ty == 0 ? Rta : Rtb;
-      float (*Ev)[32] = ty == 0 ? Eta : Etb;
-      R[0][tx] = r.h; R[1][tx] = r.l;
-      Ev[0][tx] = e.h; Ev[1][tx] = e.l;
+    if (st == 0) return;
+    const long long o_ = orow * ldd + ocol0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      t[k] = {(t[k].h * s1t) * s2t, (t[k].l * s1t) * s2t};
+      tt[k] = {(tt[k].h * s1tt) * s2tt, (tt[k].l * s1tt) * s2tt};
     }
+    put4<F8>(t, st, ts + o_, plane);
+    put4<F8>(tt, st, tts + o_, plane);
+  };
+
+  int ta = 0, tb = 0;
+  if (nt > 0) load(0, 0);
+  while (ta < nt) {
+    __syncthreads();   // the previous pair is no longer read from shared memory
+    Xs[r][c0 + 0] = make_float2(xh.x, xl.x); Xs[r][c0 + 1] = make_float2(xh.y, xl.y);
+    Xs[r][c0 + 2] = make_float2(xh.z, xl.z); Xs[r][c0 + 3] = make_float2(xh.w, xl.w);
+    Ys[r][c0 + 0] = make_float2(yh.x, yl.x); Ys[r][c0 + 1] = make_float2(yh.y, yl.y);
+    Ys[r][c0 + 2] = make_float2(yh.z, yl.z); Ys[r][c0 + 3] = make_float2(yh.w, yl.w);
     __syncthreads();
-    // (i,j) block, tile (ta, tb): T = X[a][b], Tt = 2 X[a][b] - Y[b][a]
+    const int cta = ta, ctb = tb;
+    if (++tb == nt) { ++ta; tb = ta; }
+    if (ta < nt) load(ta, tb);   // next pair in flight while this one is processed
+
+    dfl t4[4], y4[4];
+    // output tile (cta, ctb): T_ij(a,b) = X[r][c] (stored (i,j)) or Y[c][r] (stored (j,i));
+    // the partner T_ij(b,a) is the other one of the two
+    {
+      const int la = cta * 32 + r, lb = ctb * 32 + c0;
+      if (la < v && lb < vpad) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int l = ty + 8 * r;
-      const int a = ta * 32 + l, b = tb * 32 + tx;
-      if (a < v && b < v) {
-        const dfl t = {Xh[l][tx], Xl[l][tx]};
-        const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Yh[tx][l], Yl[tx][l]}));
-        put(rowI + a, colJ + b, t, tt);
-        const dfl D = d_add({Rta[0][l], Rta[1][l]}, d_neg({Etb[0][tx], Etb[1][tx]}));
-        e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
+        for (int k = 0; k < 4; ++k) {
+          const float2 x = Xs[r][c0 + k], y = Ys[c0 + k][r];
+          t4[k] = tr ? dfl{y.x, y.y} : dfl{x.x, x.y};
+          y4[k] = tr ? dfl{x.x, x.y} : dfl{y.x, y.y};
+        }
+        emit(t4, y4, rowI + la, colJ + lb, lb, !tr, rowI + la, rowJ + lb);
       }
     }
-    if (ta != tb) {
+    if (cta != ctb) {   // output tile (ctb, cta): Y[r][c] (stored (i,j)) or X[c][r]
+      const int la = ctb * 32 + r, lb = cta * 32 + c0;
+      if (la < v && lb < vpad) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int l = ty + 8 * r;
-        const int a = tb * 32 + l, b = ta * 32 + tx;
-        if (a < v && b < v) {
-          const dfl t = {Yh[l][tx], Yl[l][tx]};
-          const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Xh[tx][l], Xl[tx][l]}));
-          put(rowI + a, colJ + b, t, tt);
-          const dfl D = d_add({Rtb[0][l], Rtb[1][l]}, d_neg({Eta[0][tx], Eta[1][tx]}));
-          e_acc = d_add(e_acc, d_mul(tt, d_mul(t, D)));
+        for (int k = 0; k < 4; ++k) {
+          const float2 x = Ys[r][c0 + k], y = Xs[c0 + k][r];
+          t4[k] = tr ? dfl{y.x, y.y} : dfl{x.x, x.y};
+          y4[k] = tr ? dfl{x.x, x.y} : dfl{y.x, y.y};
         }
-      }
-    }
-    if (i != j) {
-      // (j,i) block: T_ji(a',b') = T_ij(b',a'), Tt_ji(a',b') = Tt_ij(b',a')
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int l = ty + 8 * r;
-        const int ap = tb * 32 + l, bp = ta * 32 + tx;
-        if (ap < v && bp < v) {
-          const dfl t = {Xh[tx][l], Xl[tx][l]};
-          const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Yh[l][tx], Yl[l][tx]}));
-          put(rowJ + ap, colI + bp, t, tt);
-        }
-        if (ta != tb) {
-          const int ap2 = ta * 32 + l, bp2 = tb * 32 + tx;
-          if (ap2 < v && bp2 < v) {
-            const dfl t = {Yh[tx][l], Yl[tx][l]};
-            const dfl tt = d_add({2.f * t.h, 2.f * t.l}, d_neg({Xh[l][tx], Xl[l][tx]}));
-            put(rowJ + ap2, colI + bp2, t, tt);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // zero the padding columns b in [v, vpad) of this block's rows
-  const int npad = F.vpad - v;
-  if (npad > 0) {
-    const DT z = Digit<F8>::enc(0.f);
-    for (int e = tid; e < v * npad; e += blockDim.x) {
-      const int a = e / npad, b = v + e % npad;
-      for (int p = 0; p < st; ++p) {
-        tts[p * plane + (rowI + a) * RL + colJ + b] = z;
-        ts[p * plane + (rowI + a) * RL + colJ + b] = z;
-        if (i != j) {
-          tts[p * plane + (rowJ + a) * RL + colI + b] = z;
-          ts[p * plane + (rowJ + a) * RL + colI + b] = z;
-        }
+        emit(t4, y4, rowI + la, colJ + lb, lb, !tr, rowI + la, rowJ + lb);
       }
     }
   }
@@ -367,9 +388,9 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
                     __shfl_down_sync(0xffffffffu, e_acc.l, off)};
     e_acc = d_add(e_acc, o2);
   }
-  if (tx == 0) { red_h[ty] = e_acc.h; red_l[ty] = e_acc.l; }
+  if ((tid & 31) == 0) { red_h[tid >> 5] = e_acc.h; red_l[tid >> 5] = e_acc.l; }
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && !tr) {
     double e = 0.0;
     for (int w = 0; w < 8; ++w) e += (double)red_h[w] + (double)red_l[w];
     double* ep = (double*)(ws + F.ep);
@@ -405,10 +426,32 @@ struct Layout {
 size_t esz_of(const SplitPlan& sp) { return sp.fp8 ? 1 : 2; }
 int padg(const SplitPlan& sp) { return sp.fp8 ? 16 : 8; }
 
+// Padded extent of a digit-row segment of n elements: the widest alignment up to 128 bytes
+// of digits that costs under 3 % of padding (so that row segments start on L2 line or
+// sector boundaries), at least the 16-byte TMA stride rule.
+int pad_extent(const SplitPlan& sp, int n) {
+  const int esz = (int)esz_of(sp);
+  for (int a = 128 / esz; a > padg(sp); a /= 2) {
+    const int r = rup(n, a);
+    if ((long long)(r - n) * 100 < 3LL * n) return r;
+  }
+  return rup(n, padg(sp));
+}
+
+// Row stride of a plane whose rows hold n elements of esz bytes: the smallest odd multiple of
+// 128 bytes that holds them.  Tiles that run side by side read rows a fixed number of rows
+// apart; with strides that are multiples of large powers of two their addresses coincide
+// modulo 4 KB and crowd the same L2 slices.
+long long row_stride(long long n, long long esz) {
+  long long lines = (n * esz + 127) / 128;
+  if ((lines & 1) == 0) ++lines;
+  return lines * 128 / esz;
+}
+
 Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   const size_t o = f.nocc, v = f.nvir, X = f.naux;
   const size_t esz = esz_of(sp);
-  const size_t ov = o * v, vpad = rup((int)v, padg(sp)), xpad = rup((int)X, padg(sp)), RL = o * vpad;
+  const size_t ov = o * v, vpad = pad_extent(sp, (int)v), xpad = pad_extent(sp, (int)X), RL = o * vpad;
   // digit planes of T / Tt (and B for Gamma) exist only when an output needs them
   const bool want_t = f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0;
   const size_t st_t = want_t ? (size_t)sp.slices_t : 0;
@@ -416,14 +459,16 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   Layout L{};
   size_t off = 0;
   L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * esz);
-  L.bs2 = off; off += al256(st_g * X * RL * esz);
+  const size_t ldd = (size_t)row_stride((long long)RL, (long long)esz);
+  const size_t ldt = (size_t)row_stride((long long)RL, 4);
+  L.bs2 = off; off += al256(st_g * X * ldd * esz);
   L.erow = off; off += al256(ov * 4);
   L.drow = off; off += al256(ov * 8);
   L.vdrow = off; off += al256(ov * 8);
-  L.thi = off; off += al256(ov * ov * 4);
-  L.tlo = off; off += al256(ov * ov * 4);
-  L.tts = off; off += al256(st_t * ov * RL * esz);
-  L.ts = off; off += al256(st_t * ov * RL * esz);
+  L.thi = off; off += al256(ov * ldt * 4);   // T planes: rows (i,a), columns j*vpad + b
+  L.tlo = off; off += al256(ov * ldt * 4);
+  L.tts = off; off += al256(st_t * ov * ldd * esz);
+  L.ts = off; off += al256(st_t * ov * ldd * esz);
   L.ep = off; off += al256(o * o * 8);
   L.scal = off; off += 256;
   L.total = off;
@@ -474,10 +519,12 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     const rimp2_frag& f = frags[idx];
     const Layout L = frag_layout(sp, f);
     const int o = f.nocc, v = f.nvir, X = f.naux;
-    const int ov = o * v, vpad = rup(v, padg(sp)), xpad = rup(X, padg(sp)), RL = o * vpad;
+    const int ov = o * v, vpad = pad_extent(sp, v), xpad = pad_extent(sp, X), RL = o * vpad;
     const uint64_t E2 = esz_of(sp);
+    const long long ldd = row_stride(RL, (long long)E2), ldt = row_stride(RL, 4);
     SplitFragDev s{};
     s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
+    s.ldd = ldd; s.ldt = ldt;
     s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
     s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
     s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
@@ -485,7 +532,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     s.thi = off + L.thi; s.tlo = off + L.tlo; s.tts = off + L.tts; s.ts = off + L.ts;
     s.ep = off + L.ep; s.scal = off + L.scal;
     s.pair_begin = pairs; s.row_begin = rows; s.b2_tile_begin = b2t;
-    pairs += (long long)o * (o + 1) / 2;
+    pairs += (long long)o * o;   // amplitude stage: one CTA per ordered pair
     rows += ov;
     const bool g = f.gamma_off >= 0 && X > 0 && ov > 0;
     if (g) {
@@ -515,19 +562,19 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ksplit = 1; P.k0_blocks = (X + BKv - 1) / BKv; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
-      P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ov; P.alpha = 1.0;
+      P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ldt; P.alpha = 1.0; P.vpad = vpad;
       P.d_off = s.drow; P.vd_off = s.vdrow; P.et_off = s.scal + 4; P.v = v;
       P.group_m = kVGroupRows;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
       const uint64_t str[2] = {(uint64_t)xpad * E2, (uint64_t)ov * xpad * E2};
-      const uint32_t boxA[3] = {BKv, SG_BM, 1}, boxB[3] = {BKv, (uint32_t)NTv, 1};
+      const uint32_t boxA[3] = {(uint32_t)BKv, SG_BM, 1}, boxB[3] = {(uint32_t)BKv, (uint32_t)NTv, 1};
       if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
       w.probs_v.push_back(P);
     }
-    const uint64_t plane_b = (uint64_t)ov * RL * E2;
+    const uint64_t plane_b = (uint64_t)ov * ldd * E2;
     if (g) {  // Gamma[(i,a)][Q] = sum_(j,b) Tt[(i,a)][(j,b)] B[(j,b)][Q]
       SplitProb P{};
       P.kind = PK_GAMMA; P.frag = idx;
@@ -552,10 +599,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)st};
-      const uint64_t sA[2] = {(uint64_t)RL * E2, plane_b};
+      const uint64_t sA[2] = {(uint64_t)ldd * E2, plane_b};
       const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
-      const uint64_t sB[2] = {(uint64_t)RL * E2, (uint64_t)X * RL * E2};
-      const uint32_t boxA[3] = {BKt, SG_BM, 1}, boxB[3] = {BKt, (uint32_t)NTt, 1};
+      const uint64_t sB[2] = {(uint64_t)ldd * E2, (uint64_t)X * ldd * E2};
+      const uint32_t boxA[3] = {(uint32_t)BKt, SG_BM, 1}, boxB[3] = {(uint32_t)BKt, (uint32_t)NTt, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -574,8 +621,8 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
-      const uint64_t s4[3] = {(uint64_t)RL * E2, (uint64_t)v * RL * E2, plane_b};
-      const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
+      const uint64_t s4[3] = {(uint64_t)ldd * E2, (uint64_t)v * ldd * E2, plane_b};
+      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, 1}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -594,8 +641,8 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
-      const uint64_t s5[4] = {(uint64_t)vpad * E2, (uint64_t)RL * E2, (uint64_t)v * RL * E2, plane_b};
-      const uint32_t boxA[5] = {BKt, 1, 1, SG_BM, 1}, boxB[5] = {BKt, 1, 1, (uint32_t)NTt, 1};
+      const uint64_t s5[4] = {(uint64_t)vpad * E2, (uint64_t)ldd * E2, (uint64_t)v * ldd * E2, plane_b};
+      const uint32_t boxA[5] = {(uint32_t)BKt, 1, 1, SG_BM, 1}, boxB[5] = {(uint32_t)BKt, 1, 1, (uint32_t)NTt, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -616,8 +663,8 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
-      const uint64_t s4[3] = {(uint64_t)vpad * E2, (uint64_t)RL * E2, plane_b};
-      const uint32_t boxA[4] = {BKt, SG_BM, 1, 1}, boxB[4] = {BKt, (uint32_t)NTt, 1, 1};
+      const uint64_t s4[3] = {(uint64_t)vpad * E2, (uint64_t)ldd * E2, plane_b};
+      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, 1}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, 1};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;

@@ -13,6 +13,8 @@ namespace rimp2 {
 struct SplitFragDev {
   int o, v, X, idx;
   int vpad, xpad, st_out, pad1;   // st_out: T/Tt digit slices to write (0: energy only)
+  long long ldd;    // row stride (elements) of the Tt / T / Gamma-B digit planes (>= o*vpad)
+  long long ldt;    // row stride (elements) of the double-float T planes (>= o*vpad)
   long long b_off, eo_off, ev_off;  // elements into the B / eps pools
   long long bs1;    // B digits for V: [s_v][o*v][xpad] bf16, per-row scale
   long long bs2;    // B digits for Gamma: [s_t][X][o*vpad] bf16, one scale
@@ -23,7 +25,8 @@ struct SplitFragDev {
   long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
   long long ep;     // double [o][o] pair energies
   long long scal;   // int32 [0]: exponent of the B (Gamma) scale; uint32 [1]: max |T| exponent
-  long long pair_begin, row_begin, b2_tile_begin;
+  long long pair_begin;   // first amplitude CTA of the fragment (o * o ordered pairs each)
+  long long row_begin, b2_tile_begin;
 };
 
 struct SplitPlan {
