@@ -375,11 +375,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           const int k1 = ti.k1b + kk / P->k0_blocks;
           const int x = (kk % P->k0_blocks) * BKE;
           const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
-          for (int p = 0; p < slices; ++p)
-            tma_operand(base + p * A_TILE, &P->tmA, full + st, P->a_mode, x, rowA, k1, P->div5, p);
-          for (int q = 0; q < slices; ++q)
-            tma_operand(base + slices * A_TILE + q * B_TILE, &P->tmB, full + st, P->b_mode, x, rowB,
-                        k1, P->div5, q);
+          // one box per operand covers all slices (the outermost tensor dimension): slice
+          // p of A lands at p * A_TILE, slice q of B at slices * A_TILE + q * B_TILE
+          tma_operand(base, &P->tmA, full + st, P->a_mode, x, rowA, k1, P->div5, 0);
+          tma_operand(base + slices * A_TILE, &P->tmB, full + st, P->b_mode, x, rowB, k1, P->div5,
+                      0);
           if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
         }
         if (!ok) break;

@@ -44,8 +44,8 @@ enum : int {
 constexpr int PK_RAW = 7;
 
 struct SplitProb {  // 64-byte aligned through its CUtensorMap members
-  CUtensorMap tmA;        // A slices, box {32, 128, ...}
-  CUtensorMap tmB;        // B slices, box {32, n_tile, ...}
+  CUtensorMap tmA;        // A slices, box {32, 128, ..., slices}: one copy loads all slices
+  CUtensorMap tmB;        // B slices, box {32, n_tile, ..., slices}
   int kind, frag;
   int M, N, n_tile;
   int tiles_m, tiles_n, ksplit;

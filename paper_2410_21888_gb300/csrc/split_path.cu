@@ -568,7 +568,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n;
       const uint64_t dims[3] = {(uint64_t)std::max(X, 1), (uint64_t)ov, (uint64_t)sv};
       const uint64_t str[2] = {(uint64_t)xpad * E2, (uint64_t)ov * xpad * E2};
-      const uint32_t boxA[3] = {(uint32_t)BKv, SG_BM, 1}, boxB[3] = {(uint32_t)BKv, (uint32_t)NTv, 1};
+      const uint32_t boxA[3] = {(uint32_t)BKv, SG_BM, (uint32_t)sv}, boxB[3] = {(uint32_t)BKv, (uint32_t)NTv, (uint32_t)sv};
       if (encode_tmap(&P.tmA, wsb + s.bs1, 3, dims, str, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs1, 3, dims, str, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -602,7 +602,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       const uint64_t sA[2] = {(uint64_t)ldd * E2, plane_b};
       const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
       const uint64_t sB[2] = {(uint64_t)ldd * E2, (uint64_t)X * ldd * E2};
-      const uint32_t boxA[3] = {(uint32_t)BKt, SG_BM, 1}, boxB[3] = {(uint32_t)BKt, (uint32_t)NTt, 1};
+      const uint32_t boxA[3] = {(uint32_t)BKt, SG_BM, (uint32_t)st}, boxB[3] = {(uint32_t)BKt, (uint32_t)NTt, (uint32_t)st};
       if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -622,7 +622,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s4[3] = {(uint64_t)ldd * E2, (uint64_t)v * ldd * E2, plane_b};
-      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, 1}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, 1};
+      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, (uint32_t)st}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, (uint32_t)st};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -642,7 +642,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
       const uint64_t s5[4] = {(uint64_t)vpad * E2, (uint64_t)ldd * E2, (uint64_t)v * ldd * E2, plane_b};
-      const uint32_t boxA[5] = {(uint32_t)BKt, 1, 1, SG_BM, 1}, boxB[5] = {(uint32_t)BKt, 1, 1, (uint32_t)NTt, 1};
+      const uint32_t boxA[5] = {(uint32_t)BKt, 1, 1, SG_BM, (uint32_t)st}, boxB[5] = {(uint32_t)BKt, 1, 1, (uint32_t)NTt, (uint32_t)st};
       if (encode_tmap(&P.tmA, wsb + s.tts, 5, d5, s5, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 5, d5, s5, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
@@ -664,7 +664,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
       const uint64_t s4[3] = {(uint64_t)vpad * E2, (uint64_t)ldd * E2, plane_b};
-      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, 1}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, 1};
+      const uint32_t boxA[4] = {(uint32_t)BKt, SG_BM, 1, (uint32_t)st}, boxB[4] = {(uint32_t)BKt, (uint32_t)NTt, 1, (uint32_t)st};
       if (encode_tmap(&P.tmA, wsb + s.tts, 4, d4, s4, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.ts, 4, d4, s4, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;

@@ -43,7 +43,7 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
   const uint64_t sA[2] = {(uint64_t)kpad * esz, (uint64_t)M * kpad * esz};
   const uint64_t dB[3] = {(uint64_t)(K > 0 ? K : 1), (uint64_t)N, (uint64_t)slices};
   const uint64_t sB[2] = {(uint64_t)kpad * esz, (uint64_t)N * kpad * esz};
-  const uint32_t boxA[3] = {(uint32_t)cfg.bk, SG_BM, 1}, boxB[3] = {(uint32_t)cfg.bk, (uint32_t)cfg.n_tile_max, 1};
+  const uint32_t boxA[3] = {(uint32_t)cfg.bk, SG_BM, (uint32_t)slices}, boxB[3] = {(uint32_t)cfg.bk, (uint32_t)cfg.n_tile_max, (uint32_t)slices};
   if (encode_tmap(&P.tmA, A, 3, dA, sA, boxA, esz) != RIMP2_OK ||
       encode_tmap(&P.tmB, B, 3, dB, sB, boxB, esz) != RIMP2_OK)
     return RIMP2_ERR_UNSUPPORTED;
