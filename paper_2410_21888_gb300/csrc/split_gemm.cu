@@ -273,9 +273,10 @@ __device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ pr
   ti.k1b = ks * ti.P->k1_chunk;
   ti.k1e = min(ti.P->k1_count, ti.k1b + ti.P->k1_chunk);
   ti.nK = max(0, ti.k1e - ti.k1b) * ti.P->k0_blocks;
-  // V is symmetric: tiles whose every row index exceeds every column index are covered
-  // by the mirrored writes of the transposed tile
-  ti.skip = (ti.P->kind == PK_V) && (ti.tm * SG_BM > ti.tn * nt + nt - 1);
+  // V is symmetric: only tiles with some row index >= some column index are computed.
+  // Their elements mostly lie below the diagonal and are stored through the mirror
+  // T[n][m], where the 32 rows a warp holds are 32 consecutive addresses.
+  ti.skip = (ti.P->kind == PK_V) && (ti.tm * SG_BM + SG_BM - 1 < ti.tn * nt);
   if (ti.skip) ti.nK = 0;
   return ti;
 }
@@ -598,8 +599,10 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
     c.n_tile_max = slices <= 8 ? 64 : 48;
   } else {
     c.bk = bk == 16 ? 16 : 32;
+    // 64 columns by default: with 5 or 6 slices a stage is then small enough for three
+    // stages in shared memory, which outweighs the wider MMAs of 80- or 96-column tiles
     const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
-    c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : widest;
+    c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : 64;
   }
   const size_t rowb = fp8 ? 64 : (size_t)c.bk * 2;
   const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * rowb;
