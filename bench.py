@@ -33,9 +33,11 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # dram read+write bytes per launch of the dominant kernel from an ncu capture (None until
 # measured for the current kernel); keyed by stage index
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the contraction kernel on the
-# nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture (profiles/split_gemm_c1_dram.md);
-# keyed by (precision, stage): 1 = V, 3 = Gamma/P.  Cleared whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {}
+# nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture
+# (profiles/split_path_kernels_c1_dram.md); keyed by (precision, stage): 1 = V,
+# 3 = Gamma/P.  Cleared whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {("bf16", 3): 367_517_569_280 + 15_001_098_496,
+                      ("bf16", 1): 12_071_214_080 + 10_178_675_968}
 
 
 def flops(o, v, X):

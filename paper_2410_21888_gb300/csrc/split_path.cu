@@ -93,108 +93,6 @@ template <> struct Digit<true> {
   }
 };
 
-// Digits of an FP64 value x relative to 2^E (|x| <= 2^(E-1)): X = x 2^(LB-E),
-// d_p = rint(X), X <- 2^LB (X - d_p); every step is exact in FP64.
-template <bool F8>
-__device__ __forceinline__ void digits_f64(double x, int E, int s, typename Digit<F8>::T* out,
-                                           long long plane) {
-  constexpr int LB = Digit<F8>::LB;
-  double X = ldexp(x, LB - E);
-  for (int p = 0; p < s; ++p) {
-    const double d = rint(X);
-    out[p * plane] = Digit<F8>::enc((float)d);
-    X = (X - d) * (double)(1 << LB);
-  }
-}
-
-// ------------------------------------------------------------------ kernels
-
-__global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases bs) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int* sc = (int*)((char*)bs.ws + f[i].scal);
-  sc[0] = -1000;   // below any exponent a nonzero B element can have (atomicMax target)
-  sc[1] = 0;
-}
-
-// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, the diagonal
-// V_ii(a,a) = sum_Q (B^Q_ia)^2 in FP64 and the fragment-wide maximum exponent used by the
-// Gamma operand.  The diagonal is the one element of V whose two operands have the same
-// digits: there the truncated triangle's first dropped even level holds the square of
-// the middle digit, an error of one sign that does not average out; the epilogue takes
-// this FP64 value instead.
-template <bool F8>
-__global__ void __launch_bounds__(256)
-k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, Bases bs) {
-  using DT = typename Digit<F8>::T;
-  const long long gr = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (gr >= rows) return;
-  const SplitFragDev& F = f[find_sfd(f, nf, gr, 0)];
-  const int r = (int)(gr - F.row_begin);
-  const double* x = bs.B + F.b_off + (long long)r * F.X;
-  double mx = 0.0, ss = 0.0;
-  for (int q = lane; q < F.X; q += 32) {
-    const double xq = x[q];
-    mx = fmax(mx, fabs(xq));
-    ss = fma(xq, xq, ss);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    ss += __shfl_xor_sync(0xffffffffu, ss, off);
-  }
-  const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
-  char* ws = (char*)bs.ws;
-  const long long plane = (long long)F.o * F.v * F.xpad;
-  DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
-  for (int q = lane; q < F.X; q += 32) digits_f64<F8>(x[q], E, sv, out + q, plane);
-  if (lane == 0) {
-    ((int*)(ws + F.erow))[r] = E;
-    const int i = r / F.v, a = r - i * F.v;
-    const dfl d = d_from(bs.eps[F.eo_off + i] - bs.eps[F.ev_off + a]);
-    ((float2*)(ws + F.drow))[r] = make_float2(d.h, d.l);
-    const dfl vd = d_from(ss);
-    ((float2*)(ws + F.vdrow))[r] = make_float2(vd.h, vd.l);
-    if (mx > 0.0) atomicMax((int*)(ws + F.scal), E);
-  }
-}
-
-// Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale per
-// fragment.  32 x 32 tiles transposed through shared memory.
-template <bool F8>
-__global__ void __launch_bounds__(256)
-k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
-  using DT = typename Digit<F8>::T;
-  __shared__ double tile[32][33];
-  const long long gt = blockIdx.x;
-  const SplitFragDev& F = f[find_sfd(f, nf, gt, 1)];
-  const long long lt = gt - F.b2_tile_begin;
-  const int RL = F.o * F.vpad;
-  const int ntc = (RL + 31) / 32;
-  const int tq = (int)(lt / ntc), tc = (int)(lt % ntc);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const double* B = bs.B + F.b_off;
-  for (int r = ty; r < 32; r += 8) {
-    const int c = tc * 32 + r, Q = tq * 32 + tx;
-    double val = 0.0;
-    if (c < RL && Q < F.X) {
-      const int j = c / F.vpad, b = c - j * F.vpad;
-      if (b < F.v) val = B[((long long)j * F.v + b) * F.X + Q];
-    }
-    tile[r][tx] = val;
-  }
-  __syncthreads();
-  char* ws = (char*)bs.ws;
-  const int E = *(const int*)(ws + F.scal);
-  const long long plane = (long long)F.X * F.ldd;
-  DT* out = (DT*)(ws + F.bs2);
-  for (int r = ty; r < 32; r += 8) {
-    const int Q = tq * 32 + r, c = tc * 32 + tx;
-    if (Q < F.X && c < RL) digits_f64<F8>(tile[tx][r], E, st, out + (long long)Q * F.ldd + c, plane);
-  }
-}
-
 // Four digits of one slice, packed for one store: BF16 digits are exact integers, so their
 // bit patterns are the upper halves of the FP32 values; FP8 digits go through the e4m3
 // conversion.
@@ -246,6 +144,119 @@ __device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* ou
   }
 }
 
+// Digits of an FP64 value x relative to 2^E (|x| <= 2^(E-1)), written to out[p * plane]:
+// x is split once into a double-float (48 significant bits, more than s digits carry),
+// scaled by 2^(LB-E) = s1 * s2 (two normal powers of two), and the digits are taken with
+// digit_step, exact for the double-float.
+template <bool F8>
+__device__ __forceinline__ void digits_b(double x, float s1, float s2, int s,
+                                         typename Digit<F8>::T* out, long long plane) {
+  constexpr int LB = Digit<F8>::LB;
+  const float h = (float)x;
+  const float l = (float)(x - (double)h);
+  float xh = (h * s1) * s2, xl = (l * s1) * s2;
+  for (int p = 0; p < s; ++p) out[p * plane] = Digit<F8>::enc(digit_step<LB>(xh, xl));
+}
+
+// 2^e as two normal powers of two (e clamped to [-252, 254])
+__device__ __forceinline__ void pow2_factors(int e, float& s1, float& s2) {
+  e = max(-252, min(254, e));
+  s1 = __int_as_float(((e / 2) + 127) << 23);
+  s2 = __int_as_float(((e - e / 2) + 127) << 23);
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases bs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int* sc = (int*)((char*)bs.ws + f[i].scal);
+  sc[0] = -1000;   // below any exponent a nonzero B element can have (atomicMax target)
+  sc[1] = 0;
+}
+
+// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, the diagonal
+// V_ii(a,a) = sum_Q (B^Q_ia)^2 in FP64 and the fragment-wide maximum exponent used by the
+// Gamma operand.  The diagonal is the one element of V whose two operands have the same
+// digits: there the truncated triangle's first dropped even level holds the square of
+// the middle digit, an error of one sign that does not average out; the epilogue takes
+// this FP64 value instead.
+template <bool F8>
+__global__ void __launch_bounds__(256)
+k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, Bases bs) {
+  using DT = typename Digit<F8>::T;
+  const long long gr = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gr >= rows) return;
+  const SplitFragDev& F = f[find_sfd(f, nf, gr, 0)];
+  const int r = (int)(gr - F.row_begin);
+  const double* x = bs.B + F.b_off + (long long)r * F.X;
+  double mx = 0.0, ss = 0.0;
+  for (int q = lane; q < F.X; q += 32) {
+    const double xq = x[q];
+    mx = fmax(mx, fabs(xq));
+    ss = fma(xq, xq, ss);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  }
+  const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
+  char* ws = (char*)bs.ws;
+  const long long plane = (long long)F.o * F.v * F.xpad;
+  DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
+  float s1, s2;
+  pow2_factors(Digit<F8>::LB - E, s1, s2);
+  for (int q = lane; q < F.X; q += 32) digits_b<F8>(x[q], s1, s2, sv, out + q, plane);
+  if (lane == 0) {
+    ((int*)(ws + F.erow))[r] = E;
+    const int i = r / F.v, a = r - i * F.v;
+    const dfl d = d_from(bs.eps[F.eo_off + i] - bs.eps[F.ev_off + a]);
+    ((float2*)(ws + F.drow))[r] = make_float2(d.h, d.l);
+    const dfl vd = d_from(ss);
+    ((float2*)(ws + F.vdrow))[r] = make_float2(vd.h, vd.l);
+    if (mx > 0.0) atomicMax((int*)(ws + F.scal), E);
+  }
+}
+
+// Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale per
+// fragment.  32 x 32 tiles transposed through shared memory.
+template <bool F8>
+__global__ void __launch_bounds__(256)
+k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
+  using DT = typename Digit<F8>::T;
+  __shared__ double tile[32][33];
+  const long long gt = blockIdx.x;
+  const SplitFragDev& F = f[find_sfd(f, nf, gt, 1)];
+  const long long lt = gt - F.b2_tile_begin;
+  const int RL = F.o * F.vpad;
+  const int ntc = (RL + 31) / 32;
+  const int tq = (int)(lt / ntc), tc = (int)(lt % ntc);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double* B = bs.B + F.b_off;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = tc * 32 + r, Q = tq * 32 + tx;
+    double val = 0.0;
+    if (c < RL && Q < F.X) {
+      const int j = c / F.vpad, b = c - j * F.vpad;
+      if (b < F.v) val = B[((long long)j * F.v + b) * F.X + Q];
+    }
+    tile[r][tx] = val;
+  }
+  __syncthreads();
+  char* ws = (char*)bs.ws;
+  const int E = *(const int*)(ws + F.scal);
+  const long long plane = (long long)F.X * F.ldd;
+  DT* out = (DT*)(ws + F.bs2);
+  float s1, s2;
+  pow2_factors(Digit<F8>::LB - E, s1, s2);
+  for (int r = ty; r < 32; r += 8) {
+    const int Q = tq * 32 + r, c = tc * 32 + tx;
+    if (Q < F.X && c < RL) digits_b<F8>(tile[tx][r], s1, s2, st, out + (long long)Q * F.ldd + c, plane);
+  }
+}
+
 // One CTA per ordered pair (i, j), i-major, so that the CTAs in flight fill the same rows
 // of the digit planes.  The CTA writes the (i,j) block only; it reads the stored block
 // (min(i,j), max(i,j)) of the double-float T planes (rows (i,a), columns j*vpad + b;
@@ -278,14 +289,8 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const float2* dr = (const float2*)(ws + F.drow);
   const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
   float s1t, s2t, s1tt, s2tt;   // 2^(LB - E) as two normal factors, for T and Tt
-  {
-    const int et = max(-252, min(254, LB - ((int)emax - 124)));
-    const int ett = max(-252, min(254, LB - ((int)emax - 123)));
-    s1t = __int_as_float(((et / 2) + 127) << 23);
-    s2t = __int_as_float(((et - et / 2) + 127) << 23);
-    s1tt = __int_as_float(((ett / 2) + 127) << 23);
-    s2tt = __int_as_float(((ett - ett / 2) + 127) << 23);
-  }
+  pow2_factors(LB - ((int)emax - 124), s1t, s2t);
+  pow2_factors(LB - ((int)emax - 123), s1tt, s2tt);
   DT* tts = (DT*)(ws + F.tts);
   DT* ts = (DT*)(ws + F.ts);
   const long long plane = (long long)o * v * ldd;
