@@ -97,12 +97,12 @@ typedef struct rimp2_batch {
 
 typedef struct rimp2_options {
   int32_t slices_v;    /* split modes: digit slices of B for V; 0 = default (BF16: 5
-                          slices of 8 bits, range 2..8; FP8: 8 slices of 5 bits, 2..10).
+                          slices of 8 bits, range 2..8; FP8: 8 slices of 5 bits, 2..16).
                           The diagonal V_ii(a,a) is taken from an FP64 row sum of
                           squares: there both operands have the same digits and the
                           truncated triangle's error would have one sign */
   int32_t slices_t;    /* split modes: slices for the Gamma/P operands; 0 = default
-                          (BF16: 6, range 2..8; FP8: 10, range 2..10) */
+                          (BF16: 6, range 2..8; FP8: 10, range 2..16) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
   int32_t autotune;    /* 1: the first calls of the plan each run one variant of the

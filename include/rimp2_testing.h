@@ -26,7 +26,7 @@ int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t kpad, int3
 
 /* Same with an explicit pipeline stage depth in K (BF16: stage_k = 16 for 32-byte or 32
  * for 64-byte swizzled rows) and format: fp8 != 0 takes A and B as FP8 e4m3 bytes with
- * integer values in [-16, 16], slices up to 10, kpad a multiple of 16, and
+ * integer values in [-16, 16], slices up to 16, kpad a multiple of 16, and
  *   C[m][n] = sum_{p + q < slices} 2^(-5 (p + q)) sum_k A[p][m][k] B[q][n][k]. */
 int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32_t kpad, int32_t slices,
                                int32_t stage_k, int32_t fp8, const void* A, const void* B,

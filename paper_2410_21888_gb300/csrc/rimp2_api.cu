@@ -434,7 +434,7 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   const bool fp8 = precision == RIMP2_FP8_SPLIT;
   if (o.slices_v == 0) o.slices_v = fp8 ? 8 : 5;
   if (o.slices_t == 0) o.slices_t = fp8 ? 10 : 6;
-  const int smax = fp8 ? 10 : 8;   // levels x tile width must fit the 512 TMEM columns
+  const int smax = fp8 ? 16 : 8;   // levels x tile width must fit the 512 TMEM columns
   if (precision != RIMP2_FP64 &&
       (o.slices_v < 2 || o.slices_v > smax || o.slices_t < 2 || o.slices_t > smax ||
        (o.stage_k != 0 && o.stage_k != 16 && o.stage_k != 32) ||

@@ -435,7 +435,13 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
               case 8: mma_stage<8, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
               case 9: mma_stage<9, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
               case 10: mma_stage<10, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              default: break;   // rejected by the host (slices in 2..10, slices * NT <= 512)
+              case 11: mma_stage<11, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 12: mma_stage<12, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 13: mma_stage<13, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 14: mma_stage<14, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 15: mma_stage<15, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 16: mma_stage<16, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              default: break;   // rejected by the host (slices in 2..16, slices * NT <= 512)
             }
             umma_commit(empty + st);   // frees this smem stage once its MMAs completed
             if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
@@ -596,7 +602,7 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   c.fp8 = fp8;
   if (fp8) {
     c.bk = 64;                       // 64 one-byte elements per 64-byte row
-    c.n_tile_max = slices <= 8 ? 64 : 48;
+    c.n_tile_max = slices <= 8 ? 64 : (slices <= 10 ? 48 : 32);
   } else {
     c.bk = bk == 16 ? 16 : 32;
     // 64 columns by default: with 5 or 6 slices a stage is then small enough for three
@@ -633,7 +639,7 @@ cudaError_t split_gemm_prepare() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   RIMP2_PREP(96, 64, false) RIMP2_PREP(80, 64, false) RIMP2_PREP(64, 64, false)
   RIMP2_PREP(96, 32, false) RIMP2_PREP(80, 32, false) RIMP2_PREP(64, 32, false)
-  RIMP2_PREP(64, 64, true) RIMP2_PREP(48, 64, true)
+  RIMP2_PREP(64, 64, true) RIMP2_PREP(48, 64, true) RIMP2_PREP(32, 64, true)
 #undef RIMP2_PREP
   return e;
 }
@@ -644,7 +650,8 @@ cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long to
   const int g = (int)(total_tiles < grid ? total_tiles : grid);
   if (cfg.fp8) {
     if (cfg.n_tile_max == 64) return launch_nt<64, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    return launch_nt<48, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    if (cfg.n_tile_max == 48) return launch_nt<48, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    return launch_nt<32, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
   if (cfg.bk == 32) {
     switch (cfg.n_tile_max) {

@@ -28,7 +28,7 @@ constexpr int SG_BN_MAX = 96;       // max columns per tile
 constexpr int SG_CHUNK_K = 512;     // K elements per accumulation chunk
 // K per pipeline stage: 32 (64-byte rows, 64B swizzle) or 16 (32-byte rows, 32B swizzle);
 // the smaller stage fits twice as many stages in shared memory
-constexpr int SG_MAX_SLICES = 8;
+constexpr int SG_MAX_SLICES = 16;   // FP8; BF16 stops at 8
 constexpr int SG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int SG_EPI_WARPS = 8;
 

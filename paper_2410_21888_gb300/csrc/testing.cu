@@ -19,7 +19,7 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
                                           const void* A, const void* B, double* C,
                                           void* stream) {
   if (M <= 0 || N <= 0 || K < 0 || kpad < K || kpad % (fp8 ? 16 : 8) != 0 || slices < 2 ||
-      slices > (fp8 ? 10 : 8) || !A || !B || !C)
+      slices > (fp8 ? 16 : 8) || !A || !B || !C)
     return RIMP2_ERR_BAD_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (!fp8 && stage_k != 16 && stage_k != 32) return RIMP2_ERR_BAD_ARG;

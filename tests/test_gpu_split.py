@@ -101,6 +101,7 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     (128, 64, 64, 8, 0),         # worst case magnitudes, one stage
     (200, 150, 1100, 8, 1),      # three chunks, ragged
     (130, 48, 700, 10, 2),       # ten slices, 48-column tiles
+    (140, 40, 600, 16, 3),       # sixteen slices, 32-column tiles, one pipeline stage
 ])
 def test_fp8_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
     """FP8 e4m3 digits in [-16, 16], 5-bit levels: every level sum of a chunk is exact."""
@@ -145,12 +146,14 @@ def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
     ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
     ((13, 333, 150), 8),     # Gamma's K (j,b) in two slabs, the last block past the end
 ])
-@pytest.mark.parametrize("mode", ["bf16-32", "bf16-16", "fp8"])
+@pytest.mark.parametrize("mode", ["bf16-32", "bf16-16", "fp8", "fp8-16"])
 def test_split_fragment_parity(dims, seed, mode):
     f = synth.fragment_inputs(*dims, seed=seed)
     ref = oracle.fragment(f.B, f.eo, f.ev)
     if mode == "fp8":
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8")
+    elif mode == "fp8-16":
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8", slices_v=16, slices_t=16)
     else:
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=int(mode[5:]))
     check_split(out, ref)
