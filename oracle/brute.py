@@ -36,3 +36,22 @@ def everything(B, eo, ev):
 
 def energy(B, eo, ev) -> float:
     return everything(B, eo, ev)["energy"]
+
+
+def spin_components(B, eo, ev):
+    """(E_OS, E_SS) in the spin-orbital form, independent of the spatial-orbital sums of
+    rimp2_oracle.c: the alpha-beta pairs give E_OS = sum_ijab (ia|jb)^2 / D_ijab; the
+    alpha-alpha and beta-beta pairs give, with antisymmetrised integrals
+    <ij||ab> = (ia|jb) - (ib|ja), E_SS = 2 sum_{i<j} sum_{a<b} <ij||ab>^2 / D_ijab."""
+    iajb = integrals(B)
+    D = denominators(eo, ev)
+    e_os = float(np.sum(iajb * iajb / D))
+    o, v = len(eo), len(ev)
+    e_ss = 0.0
+    for i in range(o):
+        for j in range(i + 1, o):
+            for a in range(v):
+                for b in range(a + 1, v):
+                    anti = iajb[i, a, j, b] - iajb[i, b, j, a]
+                    e_ss += 2.0 * anti * anti / D[i, a, j, b]
+    return e_os, e_ss

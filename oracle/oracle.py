@@ -55,6 +55,10 @@ def _load():
             lib.rimp2_oracle_gamma_elem.restype = d
             lib.rimp2_oracle_threads.argtypes = []
             lib.rimp2_oracle_threads.restype = i
+            lib.rimp2_oracle_spin_components.argtypes = [i, i, i, _dp, _dp, _dp, i, _dp, _dp]
+            lib.rimp2_oracle_spin_components.restype = i
+            lib.rimp2_oracle_pair_spin.argtypes = [i, i, i, _dp, _dp, _dp, i, i, _dp]
+            lib.rimp2_oracle_pair_spin.restype = i
             _lib = lib
     return _lib
 
@@ -118,6 +122,27 @@ def pab_elem(B, eo, ev, a, b, nthreads=0) -> float:
 def pij_elem(B, eo, ev, i, j, nthreads=0) -> float:
     B, eo, ev, o, v, X = _inputs(B, eo, ev)
     return _load().rimp2_oracle_pij_elem(o, v, X, _ptr(B), _ptr(eo), _ptr(ev), i, j, nthreads)
+
+
+def spin_components(B, eo, ev, nthreads=0):
+    """(E_OS, E_SS): opposite-spin sum T V and same-spin sum (T - T^T) V of one fragment
+    (E = E_OS + E_SS; SCS-MP2 is named in the paper's Introduction)."""
+    B, eo, ev, o, v, X = _inputs(B, eo, ev)
+    out = np.zeros(2)
+    rc = _load().rimp2_oracle_spin_components(o, v, X, _ptr(B), _ptr(eo), _ptr(ev), int(nthreads),
+                                               _ptr(out[0:1]), _ptr(out[1:2]))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return float(out[0]), float(out[1])
+
+
+def pair_spin(B, eo, ev, i, j):
+    """(opposite-spin, same-spin) energy of the pair (i, j)."""
+    B, eo, ev, o, v, X = _inputs(B, eo, ev)
+    out = np.zeros(2)
+    if _load().rimp2_oracle_pair_spin(o, v, X, _ptr(B), _ptr(eo), _ptr(ev), i, j, _ptr(out)) != 0:
+        raise ValueError("pair index out of range or allocation failed")
+    return float(out[0]), float(out[1])
 
 
 def algorithmic_flops(o: int, v: int, X: int) -> float:

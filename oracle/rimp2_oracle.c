@@ -257,3 +257,76 @@ double rimp2_oracle_pij_elem(int o, int v, int X, const double* B, const double*
   }
   return fail ? NAN : -s;
 }
+
+/* ---- spin components of the closed-shell energy (SCS-MP2 is named in the Introduction;
+ *      the paper prints no formula).  In spatial orbitals:
+ *        E_OS = sum_ijab T_ij(a,b) V_ij(a,b)                  opposite spin (alpha-beta)
+ *        E_SS = sum_ijab (T_ij(a,b) - T_ij(b,a)) V_ij(a,b)    same spin (alpha-alpha + beta-beta)
+ *      so that E = E_OS + E_SS.  Pair by pair, each term as defined. ---- */
+
+static void pair_spin(int v, int X, const double* B, const double* eo, const double* ev, int i,
+                      int j, double* V, nsum* os, nsum* ss) {
+  const size_t vX = (size_t)v * X;
+  pair_integrals(v, X, B + (size_t)i * vX, B + (size_t)j * vX, V);
+  for (int a = 0; a < v; ++a)
+    for (int b = 0; b < v; ++b) {
+      const double vab = V[(size_t)a * v + b];
+      const double tab = vab / (eo[i] + eo[j] - ev[a] - ev[b]);
+      const double tba = V[(size_t)b * v + a] / (eo[i] + eo[j] - ev[b] - ev[a]);
+      nadd(os, tab * vab);
+      nadd(ss, (tab - tba) * vab);
+    }
+}
+
+/* E_OS and E_SS of a fragment (either pointer may be NULL).  Returns 0 or -1. */
+int rimp2_oracle_spin_components(int o, int v, int X, const double* B, const double* eo,
+                                 const double* ev, int nthreads, double* e_os, double* e_ss) {
+  if (o < 0 || v < 0 || X < 0) return -1;
+  set_threads(nthreads);
+  const size_t vv = (size_t)v * v, np = (size_t)o * o;
+  double* pos = (double*)malloc(sizeof(double) * (np + 1));
+  double* pss = (double*)malloc(sizeof(double) * (np + 1));
+  if (!pos || !pss) { free(pos); free(pss); return -1; }
+  int bad = 0;
+#pragma omp parallel
+  {
+    double* V = (double*)malloc(sizeof(double) * (vv + 1));
+    if (!V) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic)
+    for (long long ij = 0; ij < (long long)np; ++ij) {
+      if (!V) continue;
+      nsum os = {0.0, 0.0}, ss = {0.0, 0.0};
+      pair_spin(v, X, B, eo, ev, (int)(ij / o), (int)(ij % o), V, &os, &ss);
+      pos[ij] = nval(&os);
+      pss[ij] = nval(&ss);
+    }
+    free(V);
+  }
+  nsum os = {0.0, 0.0}, ss = {0.0, 0.0};
+  for (size_t ij = 0; ij < np; ++ij) {   /* serial: thread-count independent */
+    nadd(&os, pos[ij]);
+    nadd(&ss, pss[ij]);
+  }
+  free(pos); free(pss);
+  if (bad) return -1;
+  if (e_os) *e_os = nval(&os);
+  if (e_ss) *e_ss = nval(&ss);
+  return 0;
+}
+
+/* Spin components of one pair (i, j): out[0] = opposite spin, out[1] = same spin. */
+int rimp2_oracle_pair_spin(int o, int v, int X, const double* B, const double* eo,
+                           const double* ev, int i, int j, double* out) {
+  if (i < 0 || j < 0 || i >= o || j >= o) return -1;
+  double* V = (double*)malloc(sizeof(double) * ((size_t)v * v + 1));
+  if (!V) return -1;
+  nsum os = {0.0, 0.0}, ss = {0.0, 0.0};
+  pair_spin(v, X, B, eo, ev, i, j, V, &os, &ss);
+  free(V);
+  out[0] = nval(&os);
+  out[1] = nval(&ss);
+  return 0;
+}

@@ -372,3 +372,51 @@ def test_mbe3_combine_on_three_body_function():
     mons, dims, tris = mbe.all_polymers(n)
     E = {p: f(p) for p in [(m,) for m in mons] + dims + tris}
     assert mbe.mbe3(E, mons, dims, tris) == pytest.approx(f(tuple(range(n))), rel=1e-12)
+
+
+# ---------------------------------------------------------------- spin components
+
+@pytest.mark.parametrize("dims,seed", [((3, 5, 7), 0), ((2, 4, 6), 1), ((4, 3, 5), 2)])
+def test_spin_components_vs_spin_orbital_brute_force(dims, seed):
+    """The oracle's spatial-orbital sums against the spin-orbital form (alpha-beta pairs
+    with (ia|jb)^2, same-spin pairs with antisymmetrised integrals)."""
+    B, eo, ev = frag(*dims, seed=seed)
+    e_os, e_ss = oracle.spin_components(B, eo, ev)
+    b_os, b_ss = brute.spin_components(B, eo, ev)
+    assert e_os == pytest.approx(b_os, rel=1e-12)
+    assert e_ss == pytest.approx(b_ss, rel=1e-12)
+    assert e_os + e_ss == pytest.approx(oracle.fragment(B, eo, ev, want=())["energy"], rel=1e-12)
+
+
+def test_spin_components_closed_forms_and_signs():
+    # nocc = nvir = 1: E_OS = (sum_Q B^2)^2 / (2 (e_i - e_a)) and no same-spin pair exists
+    B, eo, ev = frag(1, 1, 5)
+    e_os, e_ss = oracle.spin_components(B, eo, ev)
+    s2 = float(np.sum(B * B))
+    assert e_os == pytest.approx(s2 * s2 / (2.0 * (eo[0] - ev[0])), rel=1e-14)
+    assert e_ss == 0.0
+    # one virtual: a = b only, so E_SS = 0 exactly; one occupied: V_ii(a,b) is symmetric
+    # in (a,b), so E_SS vanishes up to the rounding of the denominators
+    B, eo, ev = frag(4, 1, 6, seed=3)
+    assert oracle.spin_components(B, eo, ev)[1] == 0.0
+    B, eo, ev = frag(1, 6, 9, seed=4)
+    e_os, e_ss = oracle.spin_components(B, eo, ev)
+    assert abs(e_ss) <= 1e-14 * abs(e_os)
+    # both components are sums of squares over negative denominators
+    for seed in range(4):
+        e_os, e_ss = oracle.spin_components(*frag(3, 5, 6, seed=seed))
+        assert e_os < 0 and e_ss < 0
+
+
+def test_pair_spin_components_sum_and_symmetry():
+    B, eo, ev = frag(3, 4, 5, seed=5)
+    pairs = {(i, j): oracle.pair_spin(B, eo, ev, i, j) for i in range(3) for j in range(3)}
+    e_os, e_ss = oracle.spin_components(B, eo, ev)
+    assert sum(p[0] for p in pairs.values()) == pytest.approx(e_os, rel=1e-13)
+    assert sum(p[1] for p in pairs.values()) == pytest.approx(e_ss, rel=1e-13)
+    for (i, j), p in pairs.items():
+        assert p[0] == pytest.approx(pairs[(j, i)][0], rel=1e-13)
+        assert p[1] == pytest.approx(pairs[(j, i)][1], rel=1e-13)
+    ep = oracle.fragment(B, eo, ev, want=("epair",))["epair"]
+    for (i, j), p in pairs.items():
+        assert p[0] + p[1] == pytest.approx(ep[i, j], rel=1e-12)
