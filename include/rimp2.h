@@ -92,7 +92,10 @@ typedef struct rimp2_batch {
   double* pij;
   double* pab;
   double* epair;
-  double* energy; /* [nfrag], required */
+  double* energy;    /* [nfrag], required: E = sum_ijab (2 T_ij(a,b) - T_ij(b,a)) V_ij(a,b) */
+  double* energy_os; /* [nfrag] or NULL: the opposite-spin component E_OS = sum T V; the
+                        same-spin one is E - E_OS (SCS-MP2, named in the paper's
+                        Introduction, weights the two components) */
 } rimp2_batch;
 
 typedef struct rimp2_options {

@@ -175,12 +175,13 @@ cudaError_t launch_gemm_f64(const GemmProb* d_probs, int nprobs, long long total
 
 // One CTA per pair block (i <= j) of one fragment.  Reads T_ij and writes
 // Tt_ij = 2 T_ij - T_ij^T for the (i,j) block and, if i != j, Tt_ji = Tt_ij^T for the
-// (j,i) block.  Pair energy e_ij = sum_ab Tt_ij(a,b) V_ij(a,b) with V = T * D.
+// (j,i) block.  Pair energy e_ij = sum_ab Tt_ij(a,b) V_ij(a,b) with V = T * D, and its
+// opposite-spin part sum_ab T_ij(a,b) V_ij(a,b).
 __global__ void __launch_bounds__(256)
 k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
   __shared__ double X[32][33];
   __shared__ double Y[32][33];
-  __shared__ double red[8];
+  __shared__ double red[8], red_os[8];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const long long gp = blockIdx.x;
   const int f = find_frag(frags, nfrag, gp, [](const FragDev& F) { return F.pair_begin; });
@@ -195,7 +196,7 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
   const double* ev = bs.eps + F.ev_off;
   const double eij = eo[i] + eo[j];
   const long long rowI = (long long)i * v, rowJ = (long long)j * v;
-  double e_part = 0.0;
+  double e_part = 0.0, e_os = 0.0;
   const int nt = (v + 31) / 32;
   const long long npairs = (long long)nt * (nt + 1) / 2;
 
@@ -223,6 +224,7 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
         if (F.tt_off >= 0) Tt[(rowI + a) * ov + rowJ + b] = tt;
         const double D = eij - ev[a] - ev[b];
         e_part += tt * (t * D);
+        e_os += t * (t * D);
       }
       if (ta != tb) {  // tile (tb, ta): Tt(a,b) = 2 Y[a][b] - X[b][a]
         const int a2 = tb * 32 + l, b2 = ta * 32 + tx;
@@ -232,6 +234,7 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
           if (F.tt_off >= 0) Tt[(rowI + a2) * ov + rowJ + b2] = tt;
           const double D = eij - ev[a2] - ev[b2];
           e_part += tt * (t * D);
+          e_os += t * (t * D);
         }
       }
     }
@@ -254,15 +257,23 @@ k_amplitude_f64(const FragDev* __restrict__ frags, int nfrag, Bases bs) {
   }
   // block reduction of the pair energy
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e_part += __shfl_down_sync(0xffffffffu, e_part, off);
-  if (tx == 0) red[ty] = e_part;
+  for (int off = 16; off > 0; off >>= 1) {
+    e_part += __shfl_down_sync(0xffffffffu, e_part, off);
+    e_os += __shfl_down_sync(0xffffffffu, e_os, off);
+  }
+  if (tx == 0) { red[ty] = e_part; red_os[ty] = e_os; }
   __syncthreads();
   if (tid == 0) {
-    double e = 0.0;
-    for (int w = 0; w < 8; ++w) e += red[w];
+    double e = 0.0, eos = 0.0;
+    for (int w = 0; w < 8; ++w) { e += red[w]; eos += red_os[w]; }
     double* ep = bs.ws + F.ep_off;
     ep[(long long)i * o + j] = e;
     ep[(long long)j * o + i] = e;
+    if (F.epos_off >= 0) {
+      double* eq = bs.ws + F.epos_off;
+      eq[(long long)i * o + j] = eos;
+      eq[(long long)j * o + i] = eos;
+    }
   }
 }
 
@@ -288,29 +299,39 @@ k_energy_reduce(const FragDev* __restrict__ frags, Bases bs) {
   __shared__ double ss[256], cc[256];
   const FragDev F = frags[blockIdx.x];
   const long long n = (long long)F.o * F.o;
-  const double* ep = bs.ws + F.ep_off;
-  double s = 0.0, c = 0.0;
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
-    const double x = ep[e];
-    double t, err;
-    two_sum(s, x, t, err);
-    s = t;
-    c += err;
-    if (F.epair_off >= 0) bs.epair[F.epair_off + e] = x;
-  }
-  ss[threadIdx.x] = s;
-  cc[threadIdx.x] = c;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
+  // compensated (TwoSum) sum of x[0..n): per-thread running sums, then a tree
+  auto csum = [&](const double* x, double* copy_to) -> double {
+    double s = 0.0, c = 0.0;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+      const double y = x[e];
       double t, err;
-      two_sum(ss[threadIdx.x], ss[threadIdx.x + w], t, err);
-      ss[threadIdx.x] = t;
-      cc[threadIdx.x] += cc[threadIdx.x + w] + err;
+      two_sum(s, y, t, err);
+      s = t;
+      c += err;
+      if (copy_to) copy_to[e] = y;
     }
+    ss[threadIdx.x] = s;
+    cc[threadIdx.x] = c;
     __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        double t, err;
+        two_sum(ss[threadIdx.x], ss[threadIdx.x + w], t, err);
+        ss[threadIdx.x] = t;
+        cc[threadIdx.x] += cc[threadIdx.x + w] + err;
+      }
+      __syncthreads();
+    }
+    const double r = ss[0] + cc[0];
+    __syncthreads();   // ss / cc are reused by the next sum
+    return r;
+  };
+  const double e = csum(bs.ws + F.ep_off, F.epair_off >= 0 ? bs.epair + F.epair_off : nullptr);
+  if (threadIdx.x == 0) bs.energy[F.idx] = e;
+  if (bs.energy_os && F.epos_off >= 0) {
+    const double eos = csum(bs.ws + F.epos_off, nullptr);
+    if (threadIdx.x == 0) bs.energy_os[F.idx] = eos;
   }
-  if (threadIdx.x == 0) bs.energy[F.idx] = ss[0] + cc[0];
 }
 
 cudaError_t launch_energy_reduce(const FragDev* d_frags, int nfrag, Bases bs, cudaStream_t s) {

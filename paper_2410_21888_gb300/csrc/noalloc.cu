@@ -85,6 +85,7 @@ extern "C" int rimp2_energy_fp64_noalloc(int32_t nocc, int32_t nvir, int32_t nau
   fd.gamma_off = fd.pij_off = fd.pab_off = -1;
   fd.epair_off = epair ? 0 : -1;
   fd.pair_begin = 0;
+  fd.epos_off = -1;
   GemmProb P{};
   long long tiles = 0;
   if (ov > 0) {

@@ -178,7 +178,9 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
     d.t_off = (long long)ws; ws += align_up(ov * ov, kAlignElems);
     d.tt_off = -1;
     if (wants_tt(f)) { d.tt_off = (long long)ws; ws += align_up(ov * ov, kAlignElems); }
-    d.ep_off = (long long)ws; ws += align_up((size_t)f.nocc * f.nocc, kAlignElems);
+    d.ep_off = (long long)ws;                  // pair energies, then opposite-spin ones
+    d.epos_off = d.ep_off + (long long)f.nocc * f.nocc;
+    ws += align_up(2 * (size_t)f.nocc * f.nocc, kAlignElems);
     d.gamma_off = f.gamma_off; d.pij_off = f.pij_off; d.pab_off = f.pab_off;
     d.epair_off = f.epair_off;
     d.pair_begin = pairs;
@@ -297,7 +299,7 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
   Bases bs{};
   bs.B = b->B; bs.eps = b->eps; bs.ws = (double*)ws;
   bs.gamma = b->gamma; bs.pij = b->pij; bs.pab = b->pab; bs.epair = b->epair;
-  bs.energy = b->energy; bs.status = p->d_status;
+  bs.energy = b->energy; bs.energy_os = b->energy_os; bs.status = p->d_status;
   int launches = 0;
   long long tiles = 0;
   if (cudaMemsetAsync(p->d_counters, 0, p->waves.size() * 8 * sizeof(unsigned), s) != cudaSuccess)
@@ -565,7 +567,7 @@ int rimp2_energy_grad(rimp2_plan* p, const rimp2_batch* b, void* workspace, size
   }
   Key k{};
   k.p[0] = b->B; k.p[1] = b->eps; k.p[2] = workspace; k.p[3] = b->gamma; k.p[4] = b->pij;
-  k.p[5] = b->pab; k.p[6] = b->epair; k.p[7] = b->energy; k.p[8] = nullptr;
+  k.p[5] = b->pab; k.p[6] = b->epair; k.p[7] = b->energy; k.p[8] = b->energy_os;
   k.frags.assign(b->frags, b->frags + b->nfrag);
   const bool changed = !p->have_desc || !(k == p->key);
   if (changed) {

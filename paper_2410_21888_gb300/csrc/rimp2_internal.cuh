@@ -36,6 +36,7 @@ struct Bases {
   double* pab;
   double* epair;
   double* energy;
+  double* energy_os;   // may be null
   unsigned* status;
 };
 
@@ -59,6 +60,7 @@ struct FragDev {
   int zero_gamma, pad0;       // 1: Gamma is accumulated by atomics, zero it first
   long long b_off, eo_off, ev_off;
   long long t_off, tt_off, ep_off;   // workspace offsets (elements)
+  long long epos_off;         // opposite-spin pair energies [o][o] (elements), or -1
   long long gamma_off, pij_off, pab_off, epair_off;  // -1: not requested
   long long pair_begin;       // prefix of o(o+1)/2 pair blocks in the wave
 };

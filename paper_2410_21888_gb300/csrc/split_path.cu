@@ -265,15 +265,16 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 // processed.  Every thread forms, for one row and four consecutive columns of the output
 // tiles (ta, tb) and (tb, ta), Tt = 2T - T^T and the digits of T and Tt (one packed store
 // per slice; columns in [nvir, vpad) get zero digits).  CTAs with i <= j also accumulate
-// the pair energy e_ij = sum_ab Tt_ij(a,b) T_ij(a,b) D_ijab in double-float (D from the
-// double-float row terms d_m = e_i - e_a).
+// the pair energy e_ij = sum_ab Tt_ij(a,b) V_ij(a,b) (V = T D) and its opposite-spin
+// part sum_ab T_ij(a,b) V_ij(a,b) in double-float (D from the double-float row terms
+// d_m = e_i - e_a).
 template <bool F8>
 __global__ void __launch_bounds__(256, 3)
 k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   using DT = typename Digit<F8>::T;
   constexpr int LB = Digit<F8>::LB;
   __shared__ float2 Xs[32][33], Ys[32][33];
-  __shared__ float red_h[8], red_l[8];
+  __shared__ float red_h[8], red_l[8], ros_h[8], ros_l[8];
   const int tid = threadIdx.x, r = tid >> 3, c0 = (tid & 7) * 4;
   const long long gp = blockIdx.x;
   const SplitFragDev& F = f[find_sfd(f, nf, gp, 2)];
@@ -298,7 +299,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const long long colJ = (long long)j * vpad;                            // output columns
   const long long rowS = (long long)i0 * v, colS = (long long)j0 * vpad; // stored block
   const int nt = (v + 31) / 32;
-  dfl e_acc = {0.f, 0.f};
+  dfl e_acc = {0.f, 0.f}, e_os = {0.f, 0.f};   // pair energy and its opposite-spin part
 
   float4 xh, xl, yh, yl;
   auto load = [&](int ta, int tb) {
@@ -331,7 +332,9 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       if (energy && ok) {
         const float2 dm = dr[drow_r], dn = dr[drow_c0 + k];
         const dfl D = d_add({dm.x, dm.y}, {dn.x, dn.y});
-        e_acc = d_add(e_acc, d_mul(tt[k], d_mul(t[k], D)));
+        const dfl V = d_mul(t[k], D);
+        e_acc = d_add(e_acc, d_mul(tt[k], V));
+        e_os = d_add(e_os, d_mul(t[k], V));
       }
     }
     if (st == 0) return;
@@ -392,15 +395,27 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
     const dfl o2 = {__shfl_down_sync(0xffffffffu, e_acc.h, off),
                     __shfl_down_sync(0xffffffffu, e_acc.l, off)};
     e_acc = d_add(e_acc, o2);
+    const dfl o3 = {__shfl_down_sync(0xffffffffu, e_os.h, off),
+                    __shfl_down_sync(0xffffffffu, e_os.l, off)};
+    e_os = d_add(e_os, o3);
   }
-  if ((tid & 31) == 0) { red_h[tid >> 5] = e_acc.h; red_l[tid >> 5] = e_acc.l; }
+  if ((tid & 31) == 0) {
+    red_h[tid >> 5] = e_acc.h; red_l[tid >> 5] = e_acc.l;
+    ros_h[tid >> 5] = e_os.h; ros_l[tid >> 5] = e_os.l;
+  }
   __syncthreads();
   if (tid == 0 && !tr) {
-    double e = 0.0;
-    for (int w = 0; w < 8; ++w) e += (double)red_h[w] + (double)red_l[w];
+    double e = 0.0, eos = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      e += (double)red_h[w] + (double)red_l[w];
+      eos += (double)ros_h[w] + (double)ros_l[w];
+    }
     double* ep = (double*)(ws + F.ep);
     ep[(long long)i * o + j] = e;
     ep[(long long)j * o + i] = e;
+    ep += (long long)o * o;          // opposite-spin pair energies
+    ep[(long long)i * o + j] = eos;
+    ep[(long long)j * o + i] = eos;
   }
 }
 
@@ -474,7 +489,7 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   L.tlo = off; off += al256(ov * ldt * 4);
   L.tts = off; off += al256(st_t * ov * ldd * esz);
   L.ts = off; off += al256(st_t * ov * ldd * esz);
-  L.ep = off; off += al256(o * o * 8);
+  L.ep = off; off += al256(2 * o * o * 8);   // pair energies, opposite-spin pair energies
   L.scal = off; off += 256;
   L.total = off;
   return L;
@@ -551,6 +566,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     d.b_off = f.b_off; d.eo_off = f.eo_off; d.ev_off = f.ev_off;
     d.t_off = d.tt_off = -1;
     d.ep_off = (long long)(s.ep / 8);
+    d.epos_off = d.ep_off + (long long)o * o;
     d.gamma_off = f.gamma_off; d.pij_off = f.pij_off; d.pab_off = f.pab_off;
     d.epair_off = f.epair_off; d.pair_begin = s.pair_begin;
     fdev.push_back(d);

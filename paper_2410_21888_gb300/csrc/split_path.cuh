@@ -23,7 +23,7 @@ struct SplitFragDev {
   long long vdrow;  // float2 [o*v]: V_ii(a,a) = sum_Q (B^Q_ia)^2 (FP64 sum) as a double-float
   long long thi, tlo;  // float [o*v][o*v]: T as a double-float pair of planes
   long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
-  long long ep;     // double [o][o] pair energies
+  long long ep;     // double [o][o] pair energies, then [o][o] opposite-spin pair energies
   long long scal;   // int32 [0]: exponent of the B (Gamma) scale; uint32 [1]: max |T| exponent
   long long pair_begin;   // first amplitude CTA of the fragment (o * o ordered pairs each)
   long long row_begin, b2_tile_begin;

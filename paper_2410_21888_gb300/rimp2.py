@@ -54,7 +54,8 @@ class Batch(ctypes.Structure):
     _fields_ = [("nfrag", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("frags", ctypes.POINTER(Frag)), ("B", ctypes.c_void_p), ("eps", ctypes.c_void_p),
                 ("gamma", ctypes.c_void_p), ("pij", ctypes.c_void_p), ("pab", ctypes.c_void_p),
-                ("epair", ctypes.c_void_p), ("energy", ctypes.c_void_p)]
+                ("epair", ctypes.c_void_p), ("energy", ctypes.c_void_p),
+                ("energy_os", ctypes.c_void_p)]
 
 
 class Options(ctypes.Structure):
@@ -234,6 +235,7 @@ class Engine:
         self.pab = torch.zeros(max(npab, 1), **f64) if want_p else None
         self.epair = torch.zeros(max(npij, 1), **f64) if want_epair else None
         self.energy = torch.zeros(max(len(self.dims), 1), **f64)
+        self.energy_os = torch.zeros(max(len(self.dims), 1), **f64)   # opposite-spin part
         ws = self.plan.workspace_size()
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
         self._frags = (Frag * max(1, len(self.dims)))()
@@ -262,6 +264,7 @@ class Engine:
         self._batch.pab = self.pab.data_ptr() if want_p else None
         self._batch.epair = self.epair.data_ptr() if want_epair else None
         self._batch.energy = self.energy.data_ptr()
+        self._batch.energy_os = self.energy_os.data_ptr()
 
     def set_inputs(self, frags, non_blocking=False):
         """frags: sequence of objects with .B [o][v][X], .eo, .ev (numpy or torch)."""
@@ -284,7 +287,7 @@ class Engine:
         """Per-fragment views of the output pools (device tensors)."""
         o, v, X = self.dims[k]
         b, e, pij, pab = self.offsets[k]
-        out = {"energy": self.energy[k]}
+        out = {"energy": self.energy[k], "energy_os": self.energy_os[k]}
         if self.gamma is not None:
             out["gamma"] = self.gamma[b:b + o * v * X].view(o, v, X)
         if self.pij is not None:
@@ -317,6 +320,12 @@ def energy_grad(B, eo, ev, precision: str = "fp64", want_gamma=True, want_p=True
         eng.check_status()
     out["engine"] = eng
     return out
+
+
+def scs_energy(energy, energy_os, c_os: float = 6.0 / 5.0, c_ss: float = 1.0 / 3.0):
+    """Spin-component-scaled MP2 energy from the library's two outputs:
+    c_os E_OS + c_ss E_SS with E_SS = E - E_OS (default weights: Grimme's SCS-MP2)."""
+    return c_os * energy_os + c_ss * (energy - energy_os)
 
 
 # ---------------------------------------------------------------- MBE3 (include/rimp2_mbe.h)

@@ -36,7 +36,8 @@ def c1():
         torch.cuda.synchronize()
         eng.check_status()
         v = eng.views(0)
-        res[prec] = {k: (t.cpu().numpy() if k != "energy" else float(t.item())) for k, t in v.items()}
+        res[prec] = {k: (float(t.item()) if k in ("energy", "energy_os") else t.cpu().numpy())
+                     for k, t in v.items()}
         del eng
         torch.cuda.empty_cache()
     return f, res
@@ -75,6 +76,9 @@ def test_c1_identities_fp64(c1):
 def test_c1_split_vs_fp64_energy(c1, prec):
     _, r = c1
     assert abs(r[prec]["energy"] - r["fp64"]["energy"]) <= 1e-7
+    # spin components: E_OS < E < 0 side by side, E_SS = E - E_OS < 0
+    assert abs(r[prec]["energy_os"] - r["fp64"]["energy_os"]) <= 1e-7
+    assert r[prec]["energy_os"] < 0 and r[prec]["energy"] - r[prec]["energy_os"] < 0
     for k in ("gamma", "pij", "pab"):
         a, b = r[prec][k], r["fp64"][k]
         assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), k
