@@ -28,12 +28,14 @@ class DeviceBlockInputs:
     block sees the same values (MBE differences cancel exactly as on the host
     generator).  Same distribution and block scaling as synth.MonomerSystem."""
 
-    def __init__(self, system):
+    def __init__(self, system, step: int = 0):
         self.s = system
+        self.step = int(step)     # time step: fresh block seeds, same geometry
         self.gen = torch.Generator(device="cuda")
 
     def _seed(self, I, J, K):
-        return zlib.crc32(np.array([self.s.seed, 97, I, J, K], dtype=np.int64).tobytes())
+        key = [self.s.seed, 97, I, J, K] + ([self.step] if self.step else [])
+        return zlib.crc32(np.array(key, dtype=np.int64).tobytes())
 
     def fill(self, eng, frags):
         s = self.s

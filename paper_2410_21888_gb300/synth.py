@@ -21,6 +21,7 @@ available, so these seeded draws stand in for them:
 """
 from __future__ import annotations
 
+import copy
 import itertools
 from dataclasses import dataclass
 
@@ -77,6 +78,14 @@ class MonomerSystem:
         self.nvir = vir_per_occ * self.nocc
         self.naux = aux_per_orb * (self.nocc + self.nvir)
         self._eps = {}
+        self.step = 0
+
+    def at_step(self, step: int) -> "MonomerSystem":
+        """The same system (geometry, orbital counts and energies) with the B blocks of
+        time step `step` (fresh seeds per step; step 0 is this system)."""
+        other = copy.copy(self)
+        other.step = int(step)
+        return other
 
     def distance(self, I: int, K: int) -> float:
         return float(np.linalg.norm(self.centroids[I] - self.centroids[K]))
@@ -97,7 +106,8 @@ class MonomerSystem:
 
     def block(self, I: int, J: int, K: int) -> np.ndarray:
         """Global-B block with occupied rows of I, virtual rows of J, aux columns of K."""
-        rng = np.random.default_rng([self.seed, _TAG_BLOCK, I, J, K])
+        key = [self.seed, _TAG_BLOCK, I, J, K] + ([self.step] if self.step else [])
+        rng = np.random.default_rng(key)
         blk = rng.normal(0.0, self.sigma,
                          size=(int(self.nocc[I]), int(self.nvir[J]), int(self.naux[K])))
         return blk * self.block_scale((I, J, K))
