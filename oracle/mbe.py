@@ -53,3 +53,37 @@ def polymers(centroids, r_dimer, r_trimer, rule="max"):
         if ok:
             trimers.append((a, b, e))
     return dimers, trimers
+
+
+def assemble(nocc, nvir, naux, fragments):
+    """MBE3 assembly of the fragments' gradient intermediates over the system's index
+    spaces (occupied, virtual and auxiliary orbitals of all monomers, monomer by monomer):
+        P_ij_sys[(I,i),(J,j)]          = sum_f c_f P_ij,f[(I,i),(J,j)]
+        P_ab_sys[(I,a),(J,b)]          = sum_f c_f P_ab,f[(I,a),(J,b)]
+        Gamma_sys[(I,J,K)][i][a][Q]    = sum_f c_f Gamma_f[(I,i)][(J,a)][(K,Q)]
+    over the fragments f containing the monomers involved.  Because E_MBE3 = sum_f c_f E_f
+    with every fragment seeing a restriction of one global B and orbital-energy set,
+    these are the MBE3 derivatives dE/dB = 4 Gamma_sys, dE/de = 2 diag(P_sys) and the
+    off-diagonal Fock couplings 4 P_sys.  The trimer coefficients are all 1 (Sec.
+    "Asynchronous time steps" accumulates trimer gradients directly for that reason).
+    `fragments`: list of (monomer tuple, coefficient, dict with gamma, pij, pab)."""
+    import numpy as np
+    nocc, nvir, naux = (np.asarray(x, dtype=int) for x in (nocc, nvir, naux))
+    oo = np.concatenate([[0], np.cumsum(nocc)])
+    vo = np.concatenate([[0], np.cumsum(nvir)])
+    pij = np.zeros((oo[-1], oo[-1]))
+    pab = np.zeros((vo[-1], vo[-1]))
+    gamma = {}
+    for mons, c, out in fragments:
+        m = list(mons)
+        fo = np.concatenate([[0], np.cumsum(nocc[m])])
+        fv = np.concatenate([[0], np.cumsum(nvir[m])])
+        fx = np.concatenate([[0], np.cumsum(naux[m])])
+        for p, I in enumerate(m):
+            for q, J in enumerate(m):
+                pij[oo[I]:oo[I + 1], oo[J]:oo[J + 1]] += c * out["pij"][fo[p]:fo[p + 1], fo[q]:fo[q + 1]]
+                pab[vo[I]:vo[I + 1], vo[J]:vo[J + 1]] += c * out["pab"][fv[p]:fv[p + 1], fv[q]:fv[q + 1]]
+                for r, K in enumerate(m):
+                    blk = gamma.setdefault((I, J, K), np.zeros((nocc[I], nvir[J], naux[K])))
+                    blk += c * out["gamma"][fo[p]:fo[p + 1], fv[q]:fv[q + 1], fx[r]:fx[r + 1]]
+    return pij, pab, gamma
