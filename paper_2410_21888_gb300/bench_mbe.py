@@ -58,7 +58,8 @@ def fill_device_inputs(eng, system, frags, gen):
         eng.eps[e + o:e + o + v].copy_(torch.from_numpy(ev))
 
 
-def run_level(frags, system, precision, device_inputs, ws_budget, reps, seed):
+def run_level(frags, system, precision, device_inputs, ws_budget, reps, seed, asm_out=None,
+              coeff=None, accumulate=False):
     eng = rimp2.Engine([system.fragment_dims(f) for f in frags], precision=precision,
                        want_epair=False, max_workspace_bytes=ws_budget)
     if device_inputs:
@@ -83,6 +84,24 @@ def run_level(frags, system, precision, device_inputs, ws_budget, reps, seed):
     energies = eng.energy[:len(frags)].cpu().numpy().copy()
     out = {"fragments": len(frags), "ms": ms, "first_call_s": first_s, "waves": st.waves,
            "launches_per_call": st.launches_per_call, "tiles_per_call": st.tiles_per_call}
+    if asm_out is not None:
+        # MBE3 assembly of this level's Gamma / P into the system arrays (added to the
+        # previous levels'), timed after one untimed pass on scratch outputs
+        offs = eng.offsets
+        asm = rimp2.MBEAssembly(system.nocc, system.nvir, system.naux, frags, coeff,
+                                [o[0] for o in offs], [o[2] for o in offs], [o[3] for o in offs])
+        g_lvl, p_lvl, q_lvl = asm.outputs()
+        asm.run(eng.gamma, eng.pij, eng.pab, g_lvl, p_lvl, q_lvl)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        asm.run(eng.gamma, eng.pij, eng.pab, g_lvl, asm_out[1], asm_out[2], accumulate=accumulate)
+        a1.record()
+        torch.cuda.synchronize()
+        n_in = sum(o * v * x + o * o + v * v for o, v, x in eng.dims)
+        out["assembly_ms"] = a0.elapsed_time(a1)
+        out["assembly_gamma_sys_elems"] = int(asm.gamma_elems)
+        out["assembly_gb_moved"] = 8.0 * (n_in + asm.gamma_elems + 2 * (asm.o_total ** 2 + asm.v_total ** 2)) / 1e9
+        del asm, g_lvl, p_lvl, q_lvl
     del eng
     torch.cuda.empty_cache()
     return out, energies
@@ -96,6 +115,8 @@ def main():
     ap.add_argument("--device-inputs", action="store_true")
     ap.add_argument("--workspace-gb", type=float, default=120.0)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--assemble", action="store_true",
+                    help="also time the MBE3 assembly of Gamma / P over the system (bf16 path)")
     a = ap.parse_args()
     system = synth.MonomerSystem(n_monomers=64, box=40.0, seed=a.seed)
     rd, rt, rule = CUTOFFS[a.cutoffs]
@@ -117,8 +138,16 @@ def main():
                 continue
             lf = [frags[k] for k in idx]
             fl = sum(flops(*system.fragment_dims(f)) for f in lf)
+            asm_out = None
+            if a.assemble and prec == "bf16":
+                if level == 1:
+                    O, V = int(np.sum(system.nocc)), int(np.sum(system.nvir))
+                    asm_state = (None, torch.zeros((O, O), dtype=torch.float64, device="cuda"),
+                                 torch.zeros((V, V), dtype=torch.float64, device="cuda"))
+                asm_out = asm_state
             r, en = run_level(lf, system, prec, a.device_inputs, int(a.workspace_gb * 2**30),
-                              a.reps if prec == "bf16" else 1, a.seed)
+                              a.reps if prec == "bf16" else 1, a.seed, asm_out=asm_out,
+                              coeff=np.asarray(coeff)[idx], accumulate=level > 1)
             E[idx] = en
             r["tflop"] = fl / 1e12
             r["tflops"] = fl / (r["ms"] * 1e-3) / 1e12

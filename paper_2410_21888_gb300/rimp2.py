@@ -348,6 +348,18 @@ def _mbe_lib():
         lib.rimp2_mbe_combine.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_void_p]
         lib.rimp2_mbe_combine.restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        lib.rimp2_assembly_create.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int64,
+                                              i32p, i32p, i64p, i64p, i64p, ctypes.POINTER(vp)]
+        lib.rimp2_assembly_create.restype = ctypes.c_int
+        lib.rimp2_assembly_sizes.argtypes = [vp, i64p, i64p, i64p]
+        lib.rimp2_assembly_sizes.restype = ctypes.c_int
+        lib.rimp2_assembly_block_index.argtypes = [vp, i64p]
+        lib.rimp2_assembly_block_index.restype = ctypes.c_int
+        lib.rimp2_assembly_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32, vp]
+        lib.rimp2_assembly_run.restype = ctypes.c_int
+        lib.rimp2_assembly_destroy.argtypes = [vp]
+        lib.rimp2_assembly_destroy.restype = None
         lib._mbe_ready = True
     return lib
 
@@ -389,6 +401,62 @@ def mbe_coefficients(n: int, dimers, trimers):
                                       nf.value, ctypes.byref(nf)), "rimp2_mbe_coefficients")
     frags = [tuple(int(x) for x in row if x >= 0) for row in fr[:nf.value]]
     return frags, co[:nf.value].copy()
+
+
+class MBEAssembly:
+    """MBE3 assembly of the fragments' Gamma, P_ij, P_ab over the system's index spaces
+    (include/rimp2_mbe.h).  `fragments`: monomer tuples in the order the fragments
+    concatenate their orbitals; offsets of each fragment's outputs in the batch pools
+    (e.g. Engine.offsets: Gamma at the B offset); -1 for no contribution."""
+
+    def __init__(self, nocc, nvir, naux, fragments, coeff, gamma_off, pij_off, pab_off):
+        lib = _mbe_lib()
+        self._lib = lib
+        self.n = len(nocc)
+        sz = [np.ascontiguousarray(np.asarray(x, dtype=np.int32)) for x in (nocc, nvir, naux)]
+        fm = np.full((len(fragments), 3), -1, dtype=np.int32)
+        for k, f in enumerate(fragments):
+            fm[k, :len(f)] = f
+        co = np.ascontiguousarray(np.asarray(coeff, dtype=np.int32))
+        offs = [np.ascontiguousarray(np.asarray(x, dtype=np.int64)) for x in (gamma_off, pij_off, pab_off)]
+        i64 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        h = ctypes.c_void_p()
+        _check(lib.rimp2_assembly_create(self.n, _i32(sz[0]), _i32(sz[1]), _i32(sz[2]), len(fragments),
+                                         _i32(fm), _i32(co), i64(offs[0]), i64(offs[1]), i64(offs[2]),
+                                         ctypes.byref(h)), "rimp2_assembly_create")
+        self._h = h
+        G, O, V = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.rimp2_assembly_sizes(h, ctypes.byref(G), ctypes.byref(O), ctypes.byref(V)),
+               "rimp2_assembly_sizes")
+        self.gamma_elems, self.o_total, self.v_total = G.value, O.value, V.value
+        idx = np.zeros(self.n ** 3, dtype=np.int64)
+        _check(lib.rimp2_assembly_block_index(h, i64(idx)), "rimp2_assembly_block_index")
+        self.block_index = idx.reshape(self.n, self.n, self.n)
+
+    def outputs(self, device="cuda"):
+        f64 = dict(dtype=torch.float64, device=device)
+        return (torch.zeros(max(self.gamma_elems, 1), **f64),
+                torch.zeros((self.o_total, self.o_total), **f64),
+                torch.zeros((self.v_total, self.v_total), **f64))
+
+    def run(self, gamma, pij, pab, gamma_sys, pij_sys, pab_sys, accumulate=False, stream=None):
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(self._lib.rimp2_assembly_run(self._h, ptr(gamma), ptr(pij), ptr(pab), ptr(gamma_sys),
+                                            ptr(pij_sys), ptr(pab_sys), int(bool(accumulate)),
+                                            _stream_handle(stream)), "rimp2_assembly_run")
+
+    def block(self, gamma_sys, I, J, K, nocc, nvir, naux):
+        off = int(self.block_index[I, J, K])
+        if off < 0:
+            return None
+        n = nocc[I] * nvir[J] * naux[K]
+        return gamma_sys[off:off + n].view(nocc[I], nvir[J], naux[K])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.rimp2_assembly_destroy(h)
+            self._h = None
 
 
 def mbe_combine(energy: torch.Tensor, coeff: torch.Tensor, stream=None) -> torch.Tensor:
