@@ -277,6 +277,8 @@ __device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ pr
   // Their elements mostly lie below the diagonal and are stored through the mirror
   // T[n][m], where the 32 rows a warp holds are 32 consecutive addresses.
   ti.skip = (ti.P->kind == PK_V) && (ti.tm * SG_BM + SG_BM - 1 < ti.tn * nt);
+  // symmetric accumulations (P_ab, P_ij): only tiles with some row <= some column
+  if (ti.P->sym) ti.skip = ti.tm * SG_BM > ti.tn * nt + nt - 1;
   if (ti.skip) ti.nK = 0;
   return ti;
 }
@@ -569,10 +571,17 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             if (n >= P->N) continue;
             const int e = ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB;
             const double val = ldexp((double)acc_h[c] + (double)acc_l[c], e);
-            if ((P->kind == PK_GAMMA || P->kind == PK_RAW) && P->ksplit == 1)
+            if ((P->kind == PK_GAMMA || P->kind == PK_RAW) && P->ksplit == 1) {
               C[(long long)m * P->ldc + n] = P->alpha * val;
-            else
+            } else if (P->sym) {
+              // each unordered pair once: (m,n) and its mirror for m < n, the diagonal once;
+              // m > n is covered by the mirror of a computed tile
+              if (m > n) continue;
               atomicAdd(C + (long long)m * P->ldc + n, P->alpha * val);
+              if (m < n) atomicAdd(C + (long long)n * P->ldc + m, P->alpha * val);
+            } else {
+              atomicAdd(C + (long long)m * P->ldc + n, P->alpha * val);
+            }
           }
         }
       }

@@ -67,7 +67,8 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
   int v;                      // PK_V: nvir of the fragment
   int group_m;                // > 1: tiles walked in groups of group_m rows, column by column
   int vpad;                   // PK_V: T plane column of (j,b) is j*vpad + b
-  int pad2;
+  int sym;                    // 1: C is symmetric (P_ab, P_ij): tiles below the diagonal are
+                              // skipped and every (m < n) result is added at (m,n) and (n,m)
 };
 
 struct SplitLaunch {

@@ -638,7 +638,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
-      P.c_off = f.pab_off; P.ldc = v; P.alpha = 1.0;
+      P.c_off = f.pab_off; P.ldc = v; P.alpha = 1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)RL, (uint64_t)v, (uint64_t)o, (uint64_t)st};
@@ -658,7 +658,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.a_mode = P.b_mode = TM_5D; P.div5 = v;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
-      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0;
+      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d5[5] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)v, (uint64_t)o, (uint64_t)st};
@@ -680,7 +680,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
       P.ea_add = -123; P.eb_add = -124;
-      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0;
+      P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       const uint64_t d4[4] = {(uint64_t)vpad, (uint64_t)o, (uint64_t)ov, (uint64_t)st};
