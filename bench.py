@@ -36,8 +36,7 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture
 # (profiles/split_path_kernels_c1_dram.md); keyed by (precision, stage): 1 = V,
 # 3 = Gamma/P.  Cleared whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {("bf16", 3): 367_517_569_280 + 15_001_098_496,
-                      ("bf16", 1): 12_071_214_080 + 10_178_675_968}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def flops(o, v, X):
