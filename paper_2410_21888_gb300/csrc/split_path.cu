@@ -259,7 +259,7 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 
 // One CTA per ordered pair (i, j), i-major, so that the CTAs in flight fill the same rows
 // of the digit planes.  The CTA writes the (i,j) block only; it reads the stored block
-// (min(i,j), max(i,j)) of the double-float T planes (rows (i,a), columns j*vpad + b;
+// (min(i,j), max(i,j)) of the double-float T planes (rows (i,a), columns j*vpadt + b;
 // T_ij(a,b) = T_ji(b,a)) in pairs of 32 x 32 tiles (ta <= tb): X = tile (ta, tb) and
 // Y = tile (tb, ta), 16-byte loads prefetched into registers while the previous pair is
 // processed.  Every thread forms, for one row and four consecutive columns of the output
@@ -297,7 +297,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const long long plane = (long long)o * v * ldd;
   const long long rowI = (long long)i * v, rowJ = (long long)j * v;      // output rows, D terms
   const long long colJ = (long long)j * vpad;                            // output columns
-  const long long rowS = (long long)i0 * v, colS = (long long)j0 * vpad; // stored block
+  const long long rowS = (long long)i0 * v, colS = (long long)j0 * F.vpadt; // stored T block
   const int nt = (v + 31) / 32;
   dfl e_acc = {0.f, 0.f}, e_os = {0.f, 0.f};   // pair energy and its opposite-spin part
 
@@ -306,13 +306,13 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     xh = xl = yh = yl = z;
     const int ax = ta * 32 + r, bx = tb * 32 + c0;
-    if (ax < v && bx < vpad) {
+    if (ax < v && bx < F.vpadt) {
       const long long ix = (rowS + ax) * ldt + colS + bx;
       xh = __ldg((const float4*)(Th + ix));
       xl = __ldg((const float4*)(Tl + ix));
     }
     const int ay = tb * 32 + r, by = ta * 32 + c0;
-    if (ay < v && by < vpad) {
+    if (ay < v && by < F.vpadt) {
       const long long iy = (rowS + ay) * ldt + colS + by;
       yh = __ldg((const float4*)(Th + iy));
       yl = __ldg((const float4*)(Tl + iy));
@@ -480,12 +480,12 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   size_t off = 0;
   L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * esz);
   const size_t ldd = (size_t)row_stride((long long)RL, (long long)esz);
-  const size_t ldt = (size_t)row_stride((long long)RL, 4);
+  const size_t ldt = (size_t)row_stride((long long)o * rup((int)v, 32), 4);
   L.bs2 = off; off += al256(st_g * X * ldd * esz);
   L.erow = off; off += al256(ov * 4);
   L.drow = off; off += al256(ov * 8);
   L.vdrow = off; off += al256(ov * 8);
-  L.thi = off; off += al256(ov * ldt * 4);   // T planes: rows (i,a), columns j*vpad + b
+  L.thi = off; off += al256(ov * ldt * 4);   // T planes: rows (i,a), columns j*vpadt + b
   L.tlo = off; off += al256(ov * ldt * 4);
   L.tts = off; off += al256(st_t * ov * ldd * esz);
   L.ts = off; off += al256(st_t * ov * ldd * esz);
@@ -541,10 +541,11 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     const int o = f.nocc, v = f.nvir, X = f.naux;
     const int ov = o * v, vpad = pad_extent(sp, v), xpad = pad_extent(sp, X), RL = o * vpad;
     const uint64_t E2 = esz_of(sp);
-    const long long ldd = row_stride(RL, (long long)E2), ldt = row_stride(RL, 4);
+    const int vpadt = rup(v, 32);
+    const long long ldd = row_stride(RL, (long long)E2), ldt = row_stride((long long)o * vpadt, 4);
     SplitFragDev s{};
     s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
-    s.ldd = ldd; s.ldt = ldt;
+    s.ldd = ldd; s.ldt = ldt; s.vpadt = vpadt;
     s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
     s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
     s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
@@ -583,7 +584,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.ksplit = 1; P.k0_blocks = (X + BKv - 1) / BKv; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 1; P.ea_off = P.eb_off = s.erow;
-      P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ldt; P.alpha = 1.0; P.vpad = vpad;
+      P.c_off = s.thi; P.c2_off = s.tlo; P.ldc = ldt; P.alpha = 1.0; P.vpad = vpadt;
       P.d_off = s.drow; P.vd_off = s.vdrow; P.et_off = s.scal + 4; P.v = v;
       P.group_m = kVGroupRows;
       P.ntiles = (long long)P.tiles_m * P.tiles_n;

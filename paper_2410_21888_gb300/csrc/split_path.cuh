@@ -12,7 +12,8 @@ namespace rimp2 {
 // Per-fragment workspace layout of the split path (byte offsets into the workspace).
 struct SplitFragDev {
   int o, v, X, idx;
-  int vpad, xpad, st_out, pad1;   // st_out: T/Tt digit slices to write (0: energy only)
+  int vpad, xpad, st_out;   // st_out: T/Tt digit slices to write (0: energy only)
+  int vpadt;                // j-block width of the T planes (nvir rounded up to 32: 128 B)
   long long ldd;    // row stride (elements) of the Tt / T / Gamma-B digit planes (>= o*vpad)
   long long ldt;    // row stride (elements) of the double-float T planes (>= o*vpad)
   long long b_off, eo_off, ev_off;  // elements into the B / eps pools
@@ -21,7 +22,7 @@ struct SplitFragDev {
   long long erow;   // int32 [o*v] row exponents of bs1
   long long drow;   // float2 [o*v]: e_i - e_a as a double-float
   long long vdrow;  // float2 [o*v]: V_ii(a,a) = sum_Q (B^Q_ia)^2 (FP64 sum) as a double-float
-  long long thi, tlo;  // float [o*v][o*v]: T as a double-float pair of planes
+  long long thi, tlo;  // float [o*v][ldt]: T as a double-float pair of planes, column j*vpadt + b
   long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
   long long ep;     // double [o][o] pair energies, then [o][o] opposite-spin pair energies
   long long scal;   // int32 [0]: exponent of the B (Gamma) scale; uint32 [1]: max |T| exponent
