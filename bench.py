@@ -234,7 +234,7 @@ def main():
 
     precs = ["bf16", "fp64"] if args.precision == "auto" else [args.precision]
     results = {}
-    e2e_ms = e2e_h2d = None
+    e2e_ms = e2e_h2d = e2e_clocks = None
     for prec in precs:
         try:
             eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True,
@@ -273,7 +273,9 @@ def main():
         st = eng.plan.stats()
         if head_run:   # end to end right after the device-timed loop, same engine
             e2e_steps = max(1, min(args.steps, 5))
-            e2e_ms, e2e_h2d = measure_e2e(eng, f, e2e_steps, barrier)
+            with ClockSampler(local) as clk_e2e:
+                e2e_ms, e2e_h2d = measure_e2e(eng, f, e2e_steps, barrier)
+            e2e_clocks = clk_e2e.summary()
         results[prec] = {"ms": ms, "steps": steps, "warmup": warm, "engine": eng,
                          "clocks": clk.summary(), "launches": st.launches_per_call,
                          "energy": float(eng.energy[0].item()), "stage_ms": stage}
@@ -333,7 +335,7 @@ def main():
                      "gamma_p_gemm": sm[3]},
         "e2e": {"value": ws * F / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": int(e2e_h2d),
-                "d2h_bytes_per_step": 8},
+                "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms, "clocks": e2e_clocks},
         "gpu_launches": int(R["launches"] * R["steps"]),
         "clocks": R["clocks"],
         "paths": {p: {"ms_per_step": r["ms"], "tflops": F / (r["ms"] * 1e-3) / 1e12,
