@@ -36,7 +36,8 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture
 # (profiles/split_path_kernels_c1_dram.md); keyed by (precision, stage): 1 = V,
 # 3 = Gamma/P.  Cleared whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {("bf16", 3): 274_771_335_936 + 14_998_897_920,
+                      ("bf16", 1): 12_169_672_960 + 10_178_702_080}
 
 
 def flops(o, v, X):
