@@ -120,10 +120,12 @@ namespace {
 
 bool wants_tt(const rimp2_frag& f) { return f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0; }
 
+// Workspace of one fragment on the FP64 path; build_fp64_wave lays out exactly this:
+// T, Tt (when an output needs it), pair energies and their opposite-spin part.
 size_t frag_ws_elems_fp64(const rimp2_frag& f) {
   const size_t ov = (size_t)f.nocc * f.nvir;
   return align_up(ov * ov, kAlignElems) * (wants_tt(f) ? 2 : 1) +
-         align_up((size_t)f.nocc * f.nocc, kAlignElems);
+         align_up(2 * (size_t)f.nocc * f.nocc, kAlignElems);
 }
 
 size_t frag_ws_elems(const rimp2_plan* p, const rimp2_frag& f) {
@@ -166,7 +168,7 @@ void finish_probs(std::vector<GemmProb>& v, long long& total) {
   }
 }
 
-void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
+int build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
   size_t ws = 0;
   long long pairs = 0;
   for (int idx : w.frags) {
@@ -245,6 +247,9 @@ void build_fp64_wave(rimp2_plan* p, const rimp2_frag* frags, WaveDesc& w) {
   w.total_pairs = pairs;
   finish_probs(w.probs_v, w.tiles_v);
   finish_probs(w.probs_c, w.tiles_c);
+  // the layout must fit the workspace the plan sized with frag_ws_elems_fp64
+  if (ws * sizeof(double) + 256 > p->ws_bytes) return RIMP2_ERR_WORKSPACE;
+  return RIMP2_OK;
 }
 
 int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags, const double* B, void* ws) {
@@ -253,8 +258,10 @@ int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags, const double* B, 
   for (auto& m : p->wave_members) {
     WaveDesc w;
     w.frags = m;
-    if (p->precision == RIMP2_FP64) build_fp64_wave(p, frags, w);
-    else {
+    if (p->precision == RIMP2_FP64) {
+      int rc = build_fp64_wave(p, frags, w);
+      if (rc != RIMP2_OK) return rc;
+    } else {
       int rc = split_build_wave(p->split, frags, m, B, ws, w.fdev, w.split, w.total_pairs, w.max_b);
       if (rc != RIMP2_OK) return rc;
     }
