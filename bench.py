@@ -30,12 +30,11 @@ WORKLOAD = {"workload": "single fragment RI-MP2 energy+Gamma+P_ab+P_ij, nocc=100
                         "naux=1500, seed 0", "nocc": 100, "nvir": 500, "naux": 1500}
 DIMS = (100, 500, 1500)
 FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)
-# dram read+write bytes per launch of the dominant kernel from an ncu capture (None until
-# measured for the current kernel); keyed by stage index
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the contraction kernel on the
-# nocc=100 nvir=500 naux=1500 fragment, one-pass ncu capture
-# (profiles/split_path_kernels_c1_dram.md); keyed by (precision, stage): 1 = V,
-# 3 = Gamma/P.  Cleared whenever the kernel changes.
+# dram__bytes_read.sum + dram__bytes_write.sum of the dominant stage's launches on the
+# nocc=100 nvir=500 naux=1500 fragment from a one-pass ncu capture
+# (profiles/split_path_kernels_c1_dram.md), keyed by (precision, stage): 1 = V (one launch),
+# 3 = Gamma/P_ab/P_ij.  An entry is removed (traffic null) whenever its kernel changes,
+# until it is captured again.
 TRAFFIC_PER_LAUNCH = {("bf16", 3): 274_771_335_936 + 14_998_897_920,
                       ("bf16", 1): 12_169_672_960 + 10_178_702_080}
 
@@ -206,7 +205,10 @@ def main():
     ap.add_argument("--stage-k", type=int, default=0, choices=[0, 16, 32],
                     help="K per tensor-core pipeline stage (0: library default)")
     ap.add_argument("--n-tile", type=int, default=0, choices=[0, 64, 80, 96])
-    ap.add_argument("--slices-t", type=int, default=0, help="0: precision default (6 for bf16)")
+    ap.add_argument("--slices-t", type=int, default=0,
+                    help="slices of the P_ab / P_ij operands; 0: precision default (6 for bf16)")
+    ap.add_argument("--slices-g", type=int, default=0,
+                    help="slices of the Gamma operands; 0: as --slices-t")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the plain FP64 path reported beside the split path")
     args = ap.parse_args()
@@ -240,7 +242,7 @@ def main():
         try:
             eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True,
                                stage_k=args.stage_k, n_tile=args.n_tile,
-                               slices_t=args.slices_t)
+                               slices_t=args.slices_t, slices_g=args.slices_g)
         except rimp2.Rimp2Error as e:
             if e.code == -8:
                 continue
@@ -308,16 +310,24 @@ def main():
     else:
         fp8 = head == "fp8"
         sv, stt = (8, args.slices_t or 10) if fp8 else (5, args.slices_t or 6)
-        prod_v, prod_t = sv * (sv + 1) // 2, stt * (stt + 1) // 2
+        sg = args.slices_g or stt
+        prod_v, prod_t, prod_g = sv * (sv + 1) // 2, stt * (stt + 1) // 2, sg * (sg + 1) // 2
+        F_g = float(2 * o * o * v * v * X)
+        F_p = F_c - F_g
         k = 3 if sm[3] >= sm[1] else 1
-        Fk = F_c * prod_t if k == 3 else F_v * prod_v
+        # stage 3: the contraction launch of Gamma, P_ab and P_ij (two launches when Gamma
+        # takes fewer slices than P)
+        Fk = F_g * prod_g + F_p * prod_t if k == 3 else F_v * prod_v
         ach = Fk / (sm[k] * 1e-3) / 1e12
         # FP8 dense peak: the measured BF16 peak x the nominal FP8:BF16 ratio (4.5 / 2.25)
         peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if fp8 else 1.0)
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get((head, k)),
-                "kernel": "k_split_gemm (" + (f"Gamma/P_ab/P_ij, {prod_t} slice products"
-                                              if k == 3 else f"V, {prod_v} slice products") + ")",
+                "kernel": "k_split_gemm (" + ((f"Gamma/P_ab/P_ij, {prod_t} slice products"
+                                               if sg == stt else
+                                               f"P_ab/P_ij, {prod_t} slice products, and Gamma, "
+                                               f"{prod_g}; 2 launches") if k == 3
+                                              else f"V, {prod_v} slice products") + ")",
                 "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)"
                                + (" x 2 (nominal fp8:bf16)" if fp8 else ""),
                 "fp64_equivalent_tflops": (F_c if k == 3 else F_v) / (sm[k] * 1e-3) / 1e12}
@@ -328,7 +338,8 @@ def main():
         "dtype": "f64" if head == "fp64" else head,
         "data": "synthetic",
         "config": dict(WORKLOAD, precision=head if head == "fp64" else
-                       (f"{head} split, {sv} slices for V, {stt} for Gamma/P"),
+                       (f"{head} split, {sv} slices for V, {stt} for Gamma/P" if sg == stt else
+                        f"{head} split, {sv} slices for V, {stt} for P_ab/P_ij, {sg} for Gamma"),
                        l2="inputs larger than L2 (B 600 MB, workspace >> 129 MB); no flush",
                        fragments_per_s=ws * 1000.0 / R["ms"], energy_Eh=R["energy"]),
         "roofline": roof,

@@ -104,8 +104,9 @@ typedef struct rimp2_options {
                           The diagonal V_ii(a,a) is taken from an FP64 row sum of
                           squares: there both operands have the same digits and the
                           truncated triangle's error would have one sign */
-  int32_t slices_t;    /* split modes: slices for the Gamma/P operands; 0 = default
-                          (BF16: 6, range 2..8; FP8: 10, range 2..16) */
+  int32_t slices_t;    /* split modes: slices of T and Tt for P_ab and P_ij (one scale
+                          per fragment); 0 = default (BF16: 6, range 2..8; FP8: 10,
+                          range 2..16) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
   int32_t autotune;    /* 1: the first calls of the plan each run one variant of the
@@ -125,6 +126,13 @@ typedef struct rimp2_options {
                                  whose key (precision, slices, shapes) is listed starts with
                                  that variant and skips the trials; new results are
                                  appended */
+  int32_t slices_g;    /* split modes: slices of the Gamma operands: the leading slices_g
+                          digit planes of Tt (one scale per fragment) and B with one scale
+                          per aux index Q; range 2..8 (BF16), 2..16 (FP8); 0 = default =
+                          slices_t, and then Gamma runs in P's launch.  Fewer slices than
+                          slices_t give a separate, cheaper Gamma launch: at the
+                          nocc=100 nvir=500 naux=1500 fragment, BF16 5 with slices_t 6
+                          measured 3.7e-10 relative Frobenius error on Gamma */
 } rimp2_options;
 
 typedef struct rimp2_stats {

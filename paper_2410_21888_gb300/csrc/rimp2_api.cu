@@ -106,8 +106,9 @@ const char* rimp2_status_string(int s) {
 void rimp2_default_options(rimp2_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
-  opt->slices_v = 0;   // 0: the precision's default (BF16 5 / 6, FP8 8 / 10)
+  opt->slices_v = 0;   // 0: the precision's default (BF16 5 / 6, FP8 8 / 10; Gamma as P)
   opt->slices_t = 0;
+  opt->slices_g = 0;
   opt->use_graph = 1;
   opt->check_inputs = 1;
   opt->autotune = 0;
@@ -379,6 +380,7 @@ uint64_t tune_key(const rimp2_plan* p) {
   h = fnv(h, (uint64_t)p->precision);
   h = fnv(h, (uint64_t)p->opt.slices_v);
   h = fnv(h, (uint64_t)p->opt.slices_t);
+  h = fnv(h, (uint64_t)p->opt.slices_g);
   h = fnv(h, (uint64_t)p->frags.size());
   for (const auto& f : p->frags) {
     h = fnv(h, ((uint64_t)f.nocc << 42) ^ ((uint64_t)f.nvir << 21) ^ (uint64_t)f.naux);
@@ -443,9 +445,11 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   const bool fp8 = precision == RIMP2_FP8_SPLIT;
   if (o.slices_v == 0) o.slices_v = fp8 ? 8 : 5;
   if (o.slices_t == 0) o.slices_t = fp8 ? 10 : 6;
+  if (o.slices_g == 0) o.slices_g = o.slices_t;
   const int smax = fp8 ? 16 : 8;   // levels x tile width must fit the 512 TMEM columns
   if (precision != RIMP2_FP64 &&
       (o.slices_v < 2 || o.slices_v > smax || o.slices_t < 2 || o.slices_t > smax ||
+       o.slices_g < 2 || o.slices_g > smax ||
        (o.stage_k != 0 && o.stage_k != 16 && o.stage_k != 32) ||
        (o.n_tile != 0 && o.n_tile != 64 && o.n_tile != 80 && o.n_tile != 96)))
     return RIMP2_ERR_UNSUPPORTED;

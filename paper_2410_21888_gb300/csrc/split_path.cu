@@ -4,14 +4,16 @@
 //   1. k_split_reset   per-fragment exponent slots
 //   2. k_slice_b1      B -> balanced base-256 digits with one scale per row (i,a): the
 //                      operands of V (Eq. MP2_ints); also d_m = e_i - e_a per row
-//   3. k_slice_b2      B -> digits with one scale per fragment, transposed to [Q][(j,b)]:
-//                      the B operand of Gamma
-//   4. split GEMM      V on the tensor cores, epilogue T = V / D kept as a double-float
-//                      pair of planes (both triangles), max |T| exponent
-//   5. k_amp_split     Tt = 2T - T^T, pair energies e_ij (FP64 per pair), digits of Tt and
+//   3. k_bcol_max      max over (j,b) of |B^Q_jb| for every aux index Q
+//   4. k_slice_b2      B -> digits with one scale per aux index Q, transposed to
+//                      [Q][(j,b)]: the B operand of Gamma
+//   5. split GEMM      V on the tensor cores, epilogue T = V / D kept as a double-float
+//                      pair of planes, max |T| exponent
+//   6. k_amp_split     Tt = 2T - T^T, pair energies e_ij (FP64 per pair), digits of Tt and
 //                      T with one scale per fragment
-//   6. energy reduce   FP64 compensated cross-pair sum (shared with the FP64 path)
-//   7. zero P, split GEMM for Gamma, P_ab and P_ij (Appendix Gamma, D^MP2_ab, D^MP2_ij)
+//   7. energy reduce   FP64 compensated cross-pair sum (shared with the FP64 path)
+//   8. zero P, split GEMMs for P_ab and P_ij, then for Gamma (Appendix Gamma, D^MP2_ab,
+//      D^MP2_ij); Gamma contracts the leading s_g digit planes of Tt
 #include <climits>
 #include <cstring>
 #include <algorithm>
@@ -71,7 +73,7 @@ __device__ __forceinline__ int find_sfd(const SplitFragDev* __restrict__ f, int 
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     const long long k = which == 0 ? f[mid].row_begin : which == 1 ? f[mid].b2_tile_begin
-                                                                   : f[mid].pair_begin;
+                        : which == 2 ? f[mid].pair_begin : f[mid].qblk_begin;
     if (k <= t) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -167,17 +169,19 @@ __device__ __forceinline__ void pow2_factors(int e, float& s1, float& s2) {
 
 // ------------------------------------------------------------------ kernels
 
+// One CTA per fragment: the atomicMax targets (max |T| exponent, column maxima of |B|)
 __global__ void k_split_reset(const SplitFragDev* __restrict__ f, int n, Bases bs) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int* sc = (int*)((char*)bs.ws + f[i].scal);
-  sc[0] = -1000;   // below any exponent a nonzero B element can have (atomicMax target)
-  sc[1] = 0;
+  const SplitFragDev& F = f[blockIdx.x];
+  char* ws = (char*)bs.ws;
+  if (threadIdx.x == 0) ((unsigned*)(ws + F.scal))[1] = 0u;
+  if (F.sg_out > 0) {
+    unsigned long long* cm = (unsigned long long*)(ws + F.ecolm);
+    for (int q = threadIdx.x; q < F.X; q += blockDim.x) cm[q] = 0ull;
+  }
 }
 
-// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m, the diagonal
-// V_ii(a,a) = sum_Q (B^Q_ia)^2 in FP64 and the fragment-wide maximum exponent used by the
-// Gamma operand.  The diagonal is the one element of V whose two operands have the same
+// One warp per row (i,a) of B: row exponent, digits of the V operand, d_m and the diagonal
+// V_ii(a,a) = sum_Q (B^Q_ia)^2 in FP64.  The diagonal is the one element of V whose two operands have the same
 // digits: there the truncated triangle's first dropped even level holds the square of
 // the middle digit, an error of one sign that does not average out; the epilogue takes
 // this FP64 value instead.
@@ -216,12 +220,42 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
     ((float2*)(ws + F.drow))[r] = make_float2(d.h, d.l);
     const dfl vd = d_from(ss);
     ((float2*)(ws + F.vdrow))[r] = make_float2(vd.h, vd.l);
-    if (mx > 0.0) atomicMax((int*)(ws + F.scal), E);
   }
 }
 
-// Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale per
-// fragment.  32 x 32 tiles transposed through shared memory.
+// Column maxima of B for Gamma's B operand: max over rows (j,b) of |B^Q_jb| for every aux
+// index Q.  One CTA per 32 aux indices x 256 rows (lane: Q, warp: every 8th row), FP64
+// bits combined by atomicMax (non-negative doubles order like their bit patterns).
+__global__ void __launch_bounds__(256)
+k_bcol_max(const SplitFragDev* __restrict__ f, int nf, Bases bs) {
+  __shared__ double red[8][32];
+  const long long gb = blockIdx.x;
+  const SplitFragDev& F = f[find_sfd(f, nf, gb, 3)];
+  const long long lb = gb - F.qblk_begin;
+  const int nqb = (F.X + 31) / 32;
+  const int qb = (int)(lb % nqb), rc = (int)(lb / nqb);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int Q = qb * 32 + lane;
+  const int r0 = rc * 256, r1 = min(F.o * F.v, r0 + 256);
+  double mx = 0.0;
+  if (Q < F.X) {
+    const double* x = bs.B + F.b_off + Q;
+#pragma unroll 8
+    for (int r = r0 + g; r < r1; r += 8) mx = fmax(mx, fabs(x[(long long)r * F.X]));
+  }
+  red[g][lane] = mx;
+  __syncthreads();
+  if (g == 0) {
+    for (int k = 1; k < 8; ++k) mx = fmax(mx, red[k][lane]);
+    if (Q < F.X && mx > 0.0)
+      atomicMax((unsigned long long*)((char*)bs.ws + F.ecolm) + Q,
+                (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale
+// 2^E_Q per aux index, E_Q = ilogb(max_(j,b) |B^Q_jb|) + 2 (also stored for the GEMM
+// epilogue).  32 x 32 tiles transposed through shared memory.
 template <bool F8>
 __global__ void __launch_bounds__(256)
 k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
@@ -246,14 +280,21 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   }
   __syncthreads();
   char* ws = (char*)bs.ws;
-  const int E = *(const int*)(ws + F.scal);
+  const unsigned long long* cm = (const unsigned long long*)(ws + F.ecolm);
+  int* ec = (int*)(ws + F.ecol);
   const long long plane = (long long)F.X * F.ldd;
   DT* out = (DT*)(ws + F.bs2);
-  float s1, s2;
-  pow2_factors(Digit<F8>::LB - E, s1, s2);
   for (int r = ty; r < 32; r += 8) {
     const int Q = tq * 32 + r, c = tc * 32 + tx;
-    if (Q < F.X && c < RL) digits_b<F8>(tile[tx][r], s1, s2, st, out + (long long)Q * F.ldd + c, plane);
+    if (Q >= F.X) continue;
+    const double mq = __longlong_as_double((long long)cm[Q]);
+    const int E = mq > 0.0 ? ilogb(mq) + 2 : -1000;
+    if (tc == 0 && tx == 0) ec[Q] = E;
+    if (c < RL) {
+      float s1, s2;
+      pow2_factors(Digit<F8>::LB - E, s1, s2);
+      digits_b<F8>(tile[tx][r], s1, s2, st, out + (long long)Q * F.ldd + c, plane);
+    }
   }
 }
 
@@ -263,8 +304,9 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 // T_ij(a,b) = T_ji(b,a)) in pairs of 32 x 32 tiles (ta <= tb): X = tile (ta, tb) and
 // Y = tile (tb, ta), 16-byte loads prefetched into registers while the previous pair is
 // processed.  Every thread forms, for one row and four consecutive columns of the output
-// tiles (ta, tb) and (tb, ta), Tt = 2T - T^T and the digits of T and Tt (one packed store
-// per slice; columns in [nvir, vpad) get zero digits).  CTAs with i <= j also accumulate
+// tiles (ta, tb) and (tb, ta), Tt = 2T - T^T and the digits of T and Tt (one scale per
+// fragment each; one packed store per slice; columns in [nvir, vpad) get zero digits).
+// CTAs with i <= j also accumulate
 // the pair energy e_ij = sum_ab Tt_ij(a,b) V_ij(a,b) (V = T D) and its opposite-spin
 // part sum_ab T_ij(a,b) V_ij(a,b) in double-float (D from the double-float row terms
 // d_m = e_i - e_a).
@@ -283,7 +325,8 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const bool tr = i > j;                  // the stored block is (j, i)
   const int i0 = tr ? j : i, j0 = tr ? i : j;
   const long long ldd = F.ldd, ldt = F.ldt;
-  st = F.st_out;           // 0: energy only, no digit planes for this fragment
+  st = F.st_out;              // Tt digit planes (0: energy only)
+  const int stt = F.st_t;     // T digit planes (0: no P)
   char* ws = (char*)bs.ws;
   const float* Th = (const float*)(ws + F.thi);
   const float* Tl = (const float*)(ws + F.tlo);
@@ -344,7 +387,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       t[k] = {(t[k].h * s1t) * s2t, (t[k].l * s1t) * s2t};
       tt[k] = {(tt[k].h * s1tt) * s2tt, (tt[k].l * s1tt) * s2tt};
     }
-    put4<F8>(t, st, ts + o_, plane);
+    put4<F8>(t, stt, ts + o_, plane);
     put4<F8>(tt, st, tts + o_, plane);
   };
 
@@ -425,9 +468,11 @@ int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.precision = precision;
   sp.slices_v = opt.slices_v;
   sp.slices_t = opt.slices_t;
+  sp.slices_g = opt.slices_g;
   sp.fp8 = precision == RIMP2_FP8_SPLIT;
   sp.cfg_v = split_launch_config(sp.slices_v, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
   sp.cfg_t = split_launch_config(sp.slices_t, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
+  sp.cfg_g = split_launch_config(sp.slices_g, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
   sp.grid = split_gemm_grid();
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   sp.ready = true;
@@ -439,7 +484,7 @@ void split_plan_release(SplitPlan&) {}
 namespace {
 
 struct Layout {
-  size_t bs1, bs2, erow, drow, vdrow, thi, tlo, tts, ts, ep, scal, total;
+  size_t bs1, bs2, erow, drow, vdrow, thi, tlo, tts, ts, ecolm, ecol, ep, scal, total;
 };
 
 // element size of the digit planes and the padding that keeps every row 16-byte aligned
@@ -472,10 +517,12 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   const size_t o = f.nocc, v = f.nvir, X = f.naux;
   const size_t esz = esz_of(sp);
   const size_t ov = o * v, vpad = pad_extent(sp, (int)v), xpad = pad_extent(sp, (int)X), RL = o * vpad;
-  // digit planes of T / Tt (and B for Gamma) exist only when an output needs them
-  const bool want_t = f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0;
-  const size_t st_t = want_t ? (size_t)sp.slices_t : 0;
-  const size_t st_g = f.gamma_off >= 0 ? (size_t)sp.slices_t : 0;
+  // digit planes exist only when an output needs them: T and Tt for P_ab and P_ij; Tt
+  // (its leading s_g planes) and B^T with one scale per aux index for Gamma
+  const bool want_p = f.pij_off >= 0 || f.pab_off >= 0;
+  const size_t st_g = f.gamma_off >= 0 ? (size_t)sp.slices_g : 0;
+  const size_t st_t = want_p ? (size_t)sp.slices_t : 0;
+  const size_t st_tt = std::max(st_t, st_g);
   Layout L{};
   size_t off = 0;
   L.bs1 = off; off += al256((size_t)sp.slices_v * ov * xpad * esz);
@@ -487,8 +534,10 @@ Layout frag_layout(const SplitPlan& sp, const rimp2_frag& f) {
   L.vdrow = off; off += al256(ov * 8);
   L.thi = off; off += al256(ov * ldt * 4);   // T planes: rows (i,a), columns j*vpadt + b
   L.tlo = off; off += al256(ov * ldt * 4);
-  L.tts = off; off += al256(st_t * ov * ldd * esz);
+  L.tts = off; off += al256(st_tt * ov * ldd * esz);
   L.ts = off; off += al256(st_t * ov * ldd * esz);
+  L.ecolm = off; off += al256(X * 8);
+  L.ecol = off; off += al256(X * 4);
   L.ep = off; off += al256(2 * o * o * 8);   // pair energies, opposite-spin pair energies
   L.scal = off; off += 256;
   L.total = off;
@@ -528,10 +577,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   (void)B;
   char* wsb = (char*)ws;
   size_t off = 0;
-  long long pairs = 0, rows = 0, b2t = 0;
-  const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max;
-  const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk;
-  const int sv = sp.slices_v, st = sp.slices_t;
+  long long pairs = 0, rows = 0, b2t = 0, qbl = 0;
+  const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max, NTg = sp.cfg_g.n_tile_max;
+  const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk, BKg = sp.cfg_g.bk;
+  const int sv = sp.slices_v, st = sp.slices_t, sgl = sp.slices_g;
   const int split_mul = sp.variant == 2 ? 4 : 2;
   const bool pij_direct = sp.variant == 1;
   w.want_gamma = false;
@@ -546,18 +595,23 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     SplitFragDev s{};
     s.o = o; s.v = v; s.X = X; s.idx = idx; s.vpad = vpad; s.xpad = xpad;
     s.ldd = ldd; s.ldt = ldt; s.vpadt = vpadt;
-    s.st_out = (f.gamma_off >= 0 || f.pij_off >= 0 || f.pab_off >= 0) ? st : 0;
+    const bool g = f.gamma_off >= 0 && X > 0 && ov > 0;
+    const bool want_p = f.pij_off >= 0 || f.pab_off >= 0;
+    s.st_t = want_p ? st : 0;
+    s.sg_out = g ? sgl : 0;
+    s.st_out = std::max(s.st_t, s.sg_out);
     s.b_off = f.b_off; s.eo_off = f.eo_off; s.ev_off = f.ev_off;
     s.bs1 = off + L.bs1; s.bs2 = off + L.bs2; s.erow = off + L.erow; s.drow = off + L.drow;
     s.vdrow = off + L.vdrow;
     s.thi = off + L.thi; s.tlo = off + L.tlo; s.tts = off + L.tts; s.ts = off + L.ts;
+    s.ecolm = off + L.ecolm; s.ecol = off + L.ecol;
     s.ep = off + L.ep; s.scal = off + L.scal;
-    s.pair_begin = pairs; s.row_begin = rows; s.b2_tile_begin = b2t;
+    s.pair_begin = pairs; s.row_begin = rows; s.b2_tile_begin = b2t; s.qblk_begin = qbl;
     pairs += (long long)o * o;   // amplitude stage: one CTA per ordered pair
     rows += ov;
-    const bool g = f.gamma_off >= 0 && X > 0 && ov > 0;
     if (g) {
       b2t += (long long)((X + 31) / 32) * ((RL + 31) / 32);
+      qbl += (long long)((X + 31) / 32) * ((ov + 255) / 256);
       w.want_gamma = true;
     }
     w.sfd.push_back(s);
@@ -600,35 +654,38 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     if (g) {  // Gamma[(i,a)][Q] = sum_(j,b) Tt[(i,a)][(j,b)] B[(j,b)][Q]
       SplitProb P{};
       P.kind = PK_GAMMA; P.frag = idx;
-      P.M = ov; P.N = X; P.n_tile = NTt;
-      P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTt - 1) / NTt;
-      P.ksplit = 1; P.k0_blocks = (RL + BKt - 1) / BKt; P.k1_count = 1; P.k1_chunk = 1;
+      P.M = ov; P.N = X; P.n_tile = NTg;
+      P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTg - 1) / NTg;
+      P.ksplit = 1; P.k0_blocks = (RL + BKg - 1) / BKg; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
       // K = (j,b) cut into slabs of about kGammaSlabK elements, slab index outermost: the
       // tiles in flight then share one slab, whose B digits stay in L2, and the tiles of a
       // row start close enough together to share their Tt rows there too
       const int kb = P.k0_blocks;
-      int slabs = sp.variant == 3 ? 1 : (int)(((long long)kb * BKt + kGammaSlabK / 2) / kGammaSlabK);
+      int slabs = sp.variant == 3 ? 1 : (int)(((long long)kb * BKg + kGammaSlabK / 2) / kGammaSlabK);
       if (slabs > 1) {
         const int per = (kb + slabs - 1) / slabs;
         slabs = (kb + per - 1) / per;
         P.k0_blocks = per; P.k1_count = slabs; P.ksplit = slabs;
-        P.a_mode = P.b_mode = TM_3DK; P.div5 = per * BKt; P.ks_outer = 1;
+        P.a_mode = P.b_mode = TM_3DK; P.div5 = per * BKg; P.ks_outer = 1;
         fdev.back().zero_gamma = 1;
       }
-      P.ea_rows = P.eb_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
-      P.eb_off = s.scal; P.eb_add = 0;
+      // the leading s_g planes of Tt (one scale per fragment) and B with one scale per aux
+      // index Q
+      P.ea_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
+      P.eb_rows = 1; P.eb_off = s.ecol; P.eb_add = 0;
       P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
-      const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)st};
+      const uint64_t dA[3] = {(uint64_t)RL, (uint64_t)ov, (uint64_t)s.st_out};
       const uint64_t sA[2] = {(uint64_t)ldd * E2, plane_b};
-      const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)st};
+      const uint64_t dB[3] = {(uint64_t)RL, (uint64_t)X, (uint64_t)sgl};
       const uint64_t sB[2] = {(uint64_t)ldd * E2, (uint64_t)X * ldd * E2};
-      const uint32_t boxA[3] = {(uint32_t)BKt, SG_BM, (uint32_t)st}, boxB[3] = {(uint32_t)BKt, (uint32_t)NTt, (uint32_t)st};
+      const uint32_t boxA[3] = {(uint32_t)BKg, SG_BM, (uint32_t)sgl}, boxB[3] = {(uint32_t)BKg, (uint32_t)NTg, (uint32_t)sgl};
       if (encode_tmap(&P.tmA, wsb + s.tts, 3, dA, sA, boxA, (int)E2) != RIMP2_OK ||
           encode_tmap(&P.tmB, wsb + s.bs2, 3, dB, sB, boxB, (int)E2) != RIMP2_OK)
         return RIMP2_ERR_UNSUPPORTED;
-      w.probs_c.push_back(P);
+      // with the slice count of P, Gamma joins P's launch
+      (sgl == st ? w.probs_c : w.probs_g).push_back(P);
     }
     if (f.pab_off >= 0) {  // P_ab = sum_i sum_(j,c) Tt[(i,a)][(j,c)] T[(i,b)][(j,c)]
       SplitProb P{};
@@ -696,8 +753,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   total_pairs = pairs;
   w.rows = rows;
   w.b2_tiles = b2t;
+  w.qblks = qbl;
   finish(w.probs_v, w.tiles_v);
   finish(w.probs_c, w.tiles_c);
+  finish(w.probs_g, w.tiles_g);
   return RIMP2_OK;
 }
 
@@ -706,6 +765,7 @@ size_t split_layout_wave(SplitWave& w, size_t off) {
   w.off_sfd = off; off = al256(off + w.sfd.size() * sizeof(SplitFragDev));
   w.off_pv = off; off = al256(off + w.probs_v.size() * sizeof(SplitProb));
   w.off_pc = off; off = al256(off + w.probs_c.size() * sizeof(SplitProb));
+  w.off_pg = off; off = al256(off + w.probs_g.size() * sizeof(SplitProb));
   return off;
 }
 
@@ -713,6 +773,7 @@ void split_fill_wave(const SplitWave& w, char* host) {
   if (!w.sfd.empty()) memcpy(host + w.off_sfd, w.sfd.data(), w.sfd.size() * sizeof(SplitFragDev));
   if (!w.probs_v.empty()) memcpy(host + w.off_pv, w.probs_v.data(), w.probs_v.size() * sizeof(SplitProb));
   if (!w.probs_c.empty()) memcpy(host + w.off_pc, w.probs_c.data(), w.probs_c.size() * sizeof(SplitProb));
+  if (!w.probs_g.empty()) memcpy(host + w.off_pg, w.probs_g.data(), w.probs_g.size() * sizeof(SplitProb));
 }
 
 int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* dfd, int nf,
@@ -721,18 +782,25 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   const SplitFragDev* sfd = (const SplitFragDev*)(dblk + w.off_sfd);
   int nl = 0;
   cudaError_t e = cudaSuccess;
-  k_split_reset<<<(nf + 127) / 128, 128, 0, s>>>(sfd, nf, bs);
-  ++nl;
-  e = cudaGetLastError();
+  if (nf > 0) {
+    k_split_reset<<<(unsigned)nf, 128, 0, s>>>(sfd, nf, bs);
+    ++nl;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && w.rows > 0) {
     if (sp.fp8) k_slice_b1<true><<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
     else k_slice_b1<false><<<(unsigned)((w.rows + 7) / 8), 256, 0, s>>>(sfd, nf, w.rows, sp.slices_v, bs);
     ++nl;
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && w.qblks > 0) {
+    k_bcol_max<<<(unsigned)w.qblks, 256, 0, s>>>(sfd, nf, bs);
+    ++nl;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && w.b2_tiles > 0) {
-    if (sp.fp8) k_slice_b2<true><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
-    else k_slice_b2<false><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_t, bs);
+    if (sp.fp8) k_slice_b2<true><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_g, bs);
+    else k_slice_b2<false><<<(unsigned)w.b2_tiles, 256, 0, s>>>(sfd, nf, sp.slices_g, bs);
     ++nl;
     e = cudaGetLastError();
   }
@@ -757,9 +825,14 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
                           ctr + 1, sp.cfg_t, sp.grid, s);
     ++nl;
   }
+  if (e == cudaSuccess && w.tiles_g > 0) {
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pg), (int)w.probs_g.size(), w.tiles_g, bs,
+                          ctr + 2, sp.cfg_g, sp.grid, s);
+    ++nl;
+  }
   if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
   *launches = nl;
-  *tiles = w.tiles_v + w.tiles_c;
+  *tiles = w.tiles_v + w.tiles_c + w.tiles_g;
   return e == cudaSuccess ? RIMP2_OK : RIMP2_ERR_CUDA;
 }
 

@@ -12,28 +12,34 @@ namespace rimp2 {
 // Per-fragment workspace layout of the split path (byte offsets into the workspace).
 struct SplitFragDev {
   int o, v, X, idx;
-  int vpad, xpad, st_out;   // st_out: T/Tt digit slices to write (0: energy only)
+  int vpad, xpad;
+  int st_out, st_t;         // digit slices to write: Tt (P and Gamma), T (P); 0: none
   int vpadt;                // j-block width of the T planes (nvir rounded up to 32: 128 B)
   long long ldd;    // row stride (elements) of the Tt / T / Gamma-B digit planes (>= o*vpad)
   long long ldt;    // row stride (elements) of the double-float T planes (>= o*vpad)
   long long b_off, eo_off, ev_off;  // elements into the B / eps pools
   long long bs1;    // B digits for V: [s_v][o*v][xpad] bf16, per-row scale
-  long long bs2;    // B digits for Gamma: [s_t][X][o*vpad] bf16, one scale
+  long long bs2;    // B digits for Gamma: [s_g][X][ldd], one scale 2^E_Q per aux index Q
   long long erow;   // int32 [o*v] row exponents of bs1
   long long drow;   // float2 [o*v]: e_i - e_a as a double-float
   long long vdrow;  // float2 [o*v]: V_ii(a,a) = sum_Q (B^Q_ia)^2 (FP64 sum) as a double-float
   long long thi, tlo;  // float [o*v][ldt]: T as a double-float pair of planes, column j*vpadt + b
-  long long tts, ts;   // Tt and T digits: [s_t][o*v][o*vpad] bf16, one scale each
+  long long tts, ts;   // Tt [st_out] and T [st_t] digit planes [s][o*v][ldd], one scale each
+                       // (Gamma reads the leading s_g planes of Tt)
+  long long ecolm;  // FP64 bits [X]: max_(j,b) |B^Q_jb| for every aux index Q
+  long long ecol;   // int32 [X]: exponent of each aux index of B for Gamma
   long long ep;     // double [o][o] pair energies, then [o][o] opposite-spin pair energies
-  long long scal;   // int32 [0]: exponent of the B (Gamma) scale; uint32 [1]: max |T| exponent
+  long long scal;   // uint32 [1]: max |T| exponent ([0] unused)
   long long pair_begin;   // first amplitude CTA of the fragment (o * o ordered pairs each)
   long long row_begin, b2_tile_begin;
+  long long qblk_begin;   // first block (32 Q x 256 rows) of the fragment in the column maxima pass
+  int sg_out, pad2;       // slices of Gamma's operands (0: no Gamma)
 };
 
 struct SplitPlan {
   int precision = 0;
-  int slices_v = 0, slices_t = 0;
-  SplitLaunch cfg_v{}, cfg_t{};
+  int slices_v = 0, slices_t = 0, slices_g = 0;
+  SplitLaunch cfg_v{}, cfg_t{}, cfg_g{};   // V; P_ab / P_ij; Gamma
   int grid = 0;
   bool ready = false;
   bool fp8 = false;  // RIMP2_FP8_SPLIT: e4m3 digits
@@ -50,10 +56,10 @@ constexpr int kSplitVariants = 4;
 
 struct SplitWave {
   std::vector<SplitFragDev> sfd;
-  std::vector<SplitProb> probs_v, probs_c;
-  long long tiles_v = 0, tiles_c = 0, rows = 0, b2_tiles = 0;
+  std::vector<SplitProb> probs_v, probs_c, probs_g;   // V; P_ab / P_ij; Gamma
+  long long tiles_v = 0, tiles_c = 0, tiles_g = 0, rows = 0, b2_tiles = 0, qblks = 0;
   bool want_gamma = false;
-  size_t off_sfd = 0, off_pv = 0, off_pc = 0;  // byte offsets in the plan device block
+  size_t off_sfd = 0, off_pv = 0, off_pc = 0, off_pg = 0;  // byte offsets in the device block
 };
 
 int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt);

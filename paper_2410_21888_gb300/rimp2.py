@@ -63,7 +63,8 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("profile_stages", ctypes.c_int32),
                 ("max_workspace_bytes", ctypes.c_size_t), ("stage_k", ctypes.c_int32),
-                ("n_tile", ctypes.c_int32), ("autotune_cache", ctypes.c_char_p)]
+                ("n_tile", ctypes.c_int32), ("autotune_cache", ctypes.c_char_p),
+                ("slices_g", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -148,7 +149,8 @@ class Plan:
                  slices_t: int = 0, use_graph: bool = True, check_inputs: bool = True,
                  max_workspace_bytes: int = 0, profile_stages: bool = False,
                  want_gamma: bool = True, want_p: bool = True, autotune: bool = False,
-                 autotune_cache: str | None = None, stage_k: int = 0, n_tile: int = 0):
+                 autotune_cache: str | None = None, stage_k: int = 0, n_tile: int = 0,
+                 slices_g: int = 0):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -159,7 +161,7 @@ class Plan:
             frags[k].gamma_off = 0 if want_gamma else -1
             frags[k].pij_off = frags[k].pab_off = 0 if want_p else -1
         opt = default_options()
-        opt.slices_v, opt.slices_t = int(slices_v), int(slices_t)
+        opt.slices_v, opt.slices_t, opt.slices_g = int(slices_v), int(slices_t), int(slices_g)
         opt.use_graph, opt.check_inputs = int(use_graph), int(check_inputs)
         opt.max_workspace_bytes = int(max_workspace_bytes)
         opt.profile_stages = int(profile_stages)

@@ -153,7 +153,8 @@ def test_split_fragment_parity(dims, seed, mode):
     if mode == "fp8":
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8")
     elif mode == "fp8-16":
-        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8", slices_v=16, slices_t=16)
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="fp8", slices_v=16, slices_t=16,
+                                slices_g=16)
     else:
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=int(mode[5:]))
     check_split(out, ref)
@@ -187,9 +188,61 @@ def test_split_error_decreases_with_slices():
     ref = oracle.fragment(f.B, f.eo, f.ev)
     errs = []
     for s in (3, 4, 6):
-        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", slices_v=s, slices_t=s)
+        out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", slices_v=s, slices_t=s,
+                                slices_g=s)
         errs.append(rel(out["gamma"].cpu().numpy(), ref["gamma"]))
     assert errs[0] > errs[1] > errs[2] or errs[2] < 1e-12, errs
+
+
+@pytest.mark.parametrize("precision,sgs", [("bf16", (2, 3, 4, 5)), ("fp8", (5, 6, 7, 8))])
+def test_gamma_slices_change_gamma_only(precision, sgs):
+    """Gamma contracts the leading s_g digit planes of Tt against its own B digits (one
+    scale per aux index): its slice count moves Gamma's error alone.  The energy does not
+    read digit planes (bit-identical); P_ab and P_ij read all s_t planes (equal up to the
+    order of their FP64 atomic sums)."""
+    f = synth.fragment_inputs(9, 70, 200, seed=13)
+    ref = oracle.fragment(f.B, f.eo, f.ev)
+    outs = [rimp2.energy_grad(f.B, f.eo, f.ev, precision=precision, slices_g=s) for s in sgs]
+    errs = [rel(o["gamma"].cpu().numpy(), ref["gamma"]) for o in outs]
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] <= TOL_A, errs
+    e0 = float(outs[0]["energy"].item())
+    for o in outs[1:]:
+        assert float(o["energy"].item()) == e0
+        for k in ("pij", "pab"):
+            a, b = o[k].cpu().numpy(), outs[0][k].cpu().numpy()
+            assert rel(a, b) <= 1e-14, k
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_gamma_zero_rows_and_aux_columns(precision):
+    """Zero rows (i,a) and a zero occupied block of B leave zero rows of V and T while Tt
+    keeps its transposed terms; a zero aux column Q takes the exponent floor as its scale
+    and gives an exactly zero Gamma column."""
+    f = synth.fragment_inputs(6, 45, 120, seed=17)
+    B = f.B.copy()
+    B[2, 7, :] = 0.0
+    B[:, :, 11] = 0.0
+    B[4, :, :] = 0.0
+    ref = oracle.fragment(B, f.eo, f.ev)
+    out = rimp2.energy_grad(B, f.eo, f.ev, precision=precision)
+    check_split(out, ref)
+    g = out["gamma"].cpu().numpy().reshape(B.shape)
+    assert np.all(g[:, :, 11] == 0.0)
+
+
+def test_gamma_rows_of_very_different_size():
+    """Virtual energies spread over three decades: rows (i,a) of T and Tt for high
+    virtuals are orders of magnitude below the fragment's largest element, whose exponent
+    sets the digit scale; the relative Frobenius errors, carried by the large rows, stay
+    within the target."""
+    rng = np.random.default_rng(23)
+    o, v, X = 8, 96, 260
+    eo = rng.uniform(-1.5, -0.3, o)
+    ev = np.sort(np.exp(rng.uniform(np.log(0.05), np.log(80.0), v)))
+    B = rng.normal(0.0, 0.05, (o, v, X))
+    ref = oracle.fragment(B, eo, ev)
+    check_split(rimp2.energy_grad(B, eo, ev, precision="bf16"), ref)
 
 
 @pytest.mark.parametrize("dims", [(4, 60, 4000), (8, 40, 2000)])
