@@ -36,6 +36,7 @@ DECAY_BOHR = 3.0
 _TAG_EPS = 11
 _TAG_BLOCK = 23
 _TAG_GEOM = 37
+_TAG_FULLMO = 41
 
 
 @dataclass
@@ -59,6 +60,44 @@ def fragment_inputs(nocc: int, nvir: int, naux: int, seed: int = 0,
     ev = rng.uniform(EPS_VIR[0], EPS_VIR[1], size=nvir)
     B = rng.normal(0.0, sigma, size=(nocc, nvir, naux))
     return FragmentInputs(np.ascontiguousarray(B), eo, ev)
+
+
+@dataclass
+class FullMOInputs:
+    """Inputs of the gradient step after the densities: the full MO-basis three-index
+    tensor Bf[p][q][Q] (occupied orbitals first, symmetric in p, q), orbital energies
+    eps[n], a symmetric positive definite J^{-1/2}[Q][P], and the fragment whose
+    occupied-virtual block Bf[i][nocc + a] is frag.B[i][a]."""
+
+    Bf: np.ndarray
+    eps: np.ndarray
+    jmh: np.ndarray
+    frag: FragmentInputs
+
+
+def full_mo_inputs(nocc: int, nvir: int, naux: int, seed: int = 0,
+                   sigma: float = B_SIGMA, jmh_range=(0.5, 2.0)) -> FullMOInputs:
+    """Seeded full-MO inputs around fragment_inputs(nocc, nvir, naux, seed): the
+    occupied-occupied and virtual-virtual blocks of B are symmetrised normal draws of
+    the same spread, J^{-1/2} = U diag(lambda) U^T with U orthogonal (QR of a normal
+    matrix) and lambda ~ U[jmh_range]."""
+    frag = fragment_inputs(nocc, nvir, naux, seed, sigma)
+    rng = np.random.default_rng([seed, _TAG_FULLMO])
+    n = nocc + nvir
+    Bf = np.zeros((n, n, naux))
+    for lo, hi in ((0, nocc), (nocc, n)):
+        m = hi - lo
+        D = rng.normal(0.0, sigma, size=(m, m, naux))
+        Bf[lo:hi, lo:hi] = (D + D.transpose(1, 0, 2)) / np.sqrt(2.0)
+    Bf[:nocc, nocc:] = frag.B
+    Bf[nocc:, :nocc] = frag.B.transpose(1, 0, 2)
+    U, R = np.linalg.qr(rng.normal(size=(naux, naux)) if naux > 0 else np.zeros((0, 0)))
+    U = U * np.sign(np.diag(R))[None, :] if naux > 0 else U
+    lam = rng.uniform(jmh_range[0], jmh_range[1], size=naux)
+    jmh = (U * lam[None, :]) @ U.T
+    jmh = 0.5 * (jmh + jmh.T)
+    eps = np.concatenate([frag.eo, frag.ev])
+    return FullMOInputs(np.ascontiguousarray(Bf), eps, np.ascontiguousarray(jmh), frag)
 
 
 class MonomerSystem:
