@@ -98,3 +98,51 @@ def gradient_chain(Bf, eps, gamma, pij, pab, jmh, nocc):
     Lp, Lpp = lagrangian(gamma, Bf, jmh, nocc)
     return {"gamma_p": gamma_aux(gamma, jmh), "lp": Lp, "lpp": Lpp,
             "dai": solve_dai(Bf, eps, gamma, pij, pab, jmh, nocc)}
+
+
+# ------------------------------------------------------------------ matrix-free forms
+# For fragments too large for the dense system: the same operator and right-hand side
+# contracted term by term (pinned against zvector_system in tests/test_zvector_pins.py).
+
+def zvector_apply(Bf, eps, x, nocc):
+    """(A x)_ia = (e_a - e_i)/2 x_ia + sum_bj [2 (ai|bj) - (aj|bi)] x_jb for x[i][a]."""
+    o = nocc
+    Bov = Bf[:o, o:, :]                                            # B^Q_ia
+    coul = np.einsum("iaQ,Q->ia", Bov, np.einsum("jbQ,jb->Q", Bov, x, optimize=True),
+                     optimize=True)
+    W = np.einsum("ibQ,jb->ijQ", Bov, x, optimize=True)            # sum_b B^Q_ib x_jb
+    exch = np.einsum("jaQ,ijQ->ia", Bov, W, optimize=True)         # sum_jQ B^Q_ja W^Q_ij
+    gap = eps[None, o:] - eps[:o, None]
+    return 0.5 * gap * x + 2.0 * coul - exch
+
+
+def zvector_rhs(Bf, gamma, pij, pab, nocc):
+    """L''_ai - L'_ia - sum_pq G^{pq}_ai Dbar_pq at [i][a], with L', L'' in their MO-B form
+    (sum_Q Gamma^Q B^Q, equal to the three-centre form since J^{-1/2} J^{1/2} = 1)."""
+    o = nocc
+    Bov, Boo, Bvv = Bf[:o, o:, :], Bf[:o, :o, :], Bf[o:, o:, :]
+    Lp_ia = np.einsum("icQ,acQ->ia", gamma, Bvv, optimize=True)    # L'_ia = sum_cQ G^Q_ic B^Q_ac
+    Lpp_ai = np.einsum("jaQ,jiQ->ia", gamma, Boo, optimize=True)   # L''_ai = sum_jQ G^Q_ja B^Q_ji
+    d = np.einsum("klQ,kl->Q", Boo, pij, optimize=True)
+    e = np.einsum("bcQ,bc->Q", Bvv, pab, optimize=True)
+    U = np.einsum("ikQ,kl->ilQ", Boo, pij, optimize=True)
+    V = np.einsum("ibQ,bc->icQ", Bov, pab, optimize=True)
+    g_oo = 2.0 * np.einsum("iaQ,Q->ia", Bov, d, optimize=True) - \
+        np.einsum("laQ,ilQ->ia", Bov, U, optimize=True)
+    g_vv = 2.0 * np.einsum("iaQ,Q->ia", Bov, e, optimize=True) - \
+        np.einsum("acQ,icQ->ia", Bvv, V, optimize=True)
+    return Lpp_ai - Lp_ia - g_oo - g_vv
+
+
+def lagrangian_elem(gamma, Bf, jmh, nocc, which, row, q):
+    """One element L'_{row,q} (which = "lp", row = i) or L''_{row,q} (which = "lpp",
+    row = a) from the three-centre form, for fragments too large for lagrangian()."""
+    o = nocc
+    jh = np.linalg.inv(jmh)
+    if which == "lp":
+        gP = gamma[row] @ jmh.T                                    # Gamma^P_ia, [a][P]
+        T3 = Bf[q, o:, :] @ jh                                     # (P|q a), [a][P]
+        return float(np.sum(gP * T3))
+    gP = gamma[:, row, :] @ jmh.T                                  # Gamma^P_ia for all i, [i][P]
+    T3 = Bf[:o, q, :] @ jh                                         # (P|i q), [i][P]
+    return float(np.sum(gP * T3))

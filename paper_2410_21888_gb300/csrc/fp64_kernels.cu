@@ -44,11 +44,12 @@ __device__ __forceinline__ int find_frag(const FragDev* __restrict__ frags, int 
 
 __global__ void __launch_bounds__(256, 2)
 k_gemm_f64(const GemmProb* __restrict__ probs, int nprobs, long long total, Bases bs,
-           unsigned* __restrict__ counter) {
+           unsigned* __restrict__ counter, const int* __restrict__ skip) {
   __shared__ double As[F64_BK][F64_BM + 1];
   __shared__ double Bs[F64_BK][F64_BN + 1];
   __shared__ long long s_tile;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (skip && *(volatile const int*)skip) return;
 
   for (;;) {
     if (tid == 0) s_tile = (long long)atomicAdd(counter, 1u);
@@ -63,8 +64,9 @@ k_gemm_f64(const GemmProb* __restrict__ probs, int nprobs, long long total, Base
     if (P.kind == PK_V) tri_index(tt, tm, tn);
     else { tm = (int)(tt / P.tiles_n); tn = (int)(tt % P.tiles_n); }
     const int m0 = tm * F64_BM, n0 = tn * F64_BN;
-    const double* __restrict__ A = (P.kind == PK_V ? bs.B : bs.ws) + P.a_off;
-    const double* __restrict__ Bo = (P.b_from_B ? bs.B : bs.ws) + P.b_off;
+    const double* __restrict__ A =
+        P.kind == PK_GEN ? P.pa : (P.kind == PK_V ? bs.B : bs.ws) + P.a_off;
+    const double* __restrict__ Bo = P.kind == PK_GEN ? P.pb : (P.b_from_B ? bs.B : bs.ws) + P.b_off;
     const bool a_kc = (P.sAk == 1), b_kc = (P.sBk == 1);
 
     double acc[4][4];
@@ -134,8 +136,11 @@ k_gemm_f64(const GemmProb* __restrict__ probs, int nprobs, long long total, Base
         }
       }
     } else {
-      double* __restrict__ C = (P.kind == PK_GAMMA ? bs.gamma : P.kind == PK_PAB ? bs.pab : bs.pij)
-                               + P.c_off;
+      double* __restrict__ C =
+          P.kind == PK_GEN ? P.pc
+                           : (P.kind == PK_GAMMA ? bs.gamma : P.kind == PK_PAB ? bs.pab : bs.pij) +
+                                 P.c_off;
+      const bool store = P.ksplit == 1 && (P.kind == PK_GAMMA || (P.kind == PK_GEN && !P.accumulate));
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int m = m0 + ty + 16 * r;
@@ -145,7 +150,7 @@ k_gemm_f64(const GemmProb* __restrict__ probs, int nprobs, long long total, Base
           const int n = n0 + tx + 16 * c;
           if (n >= P.N) continue;
           const double val = P.alpha * acc[r][c];
-          if (P.ksplit == 1 && P.kind == PK_GAMMA) C[(long long)m * P.ldc + n] = val;
+          if (store) C[(long long)m * P.ldc + n] = val;
           else atomicAdd(C + (long long)m * P.ldc + n, val);
         }
       }
@@ -164,10 +169,11 @@ int gemm_f64_occupancy_grid() {
 }
 
 cudaError_t launch_gemm_f64(const GemmProb* d_probs, int nprobs, long long total_tiles,
-                            Bases bs, unsigned* counter, int grid, cudaStream_t s) {
+                            Bases bs, unsigned* counter, int grid, cudaStream_t s,
+                            const int* skip) {
   if (total_tiles <= 0) return cudaSuccess;
   const long long g = total_tiles < grid ? total_tiles : grid;
-  k_gemm_f64<<<(unsigned)g, 256, 0, s>>>(d_probs, nprobs, total_tiles, bs, counter);
+  k_gemm_f64<<<(unsigned)g, 256, 0, s>>>(d_probs, nprobs, total_tiles, bs, counter, skip);
   return cudaGetLastError();
 }
 

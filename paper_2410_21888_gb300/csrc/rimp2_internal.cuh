@@ -23,6 +23,7 @@ enum ProbKind : int {
   PK_GAMMA = 1,  // Gamma[(i,a)][Q] = sum_(j,b) Tt[(i,a)][(j,b)] B[(j,b)][Q]
   PK_PAB = 2,    // P_ab += sum_i sum_(j,c) Tt[i][a][(j,c)] T[i][b][(j,c)]
   PK_PIJ = 3,    // P_ij += -sum_(k,b) sum_a Tt[k][b][i][a] T[k][b][j][a]
+  PK_GEN = 4,    // C = alpha A Bop^T on caller pointers pa / pb / pc (gradient step)
 };
 
 // Base pointers of one call.  Problem descriptors hold element offsets only, so a
@@ -52,6 +53,10 @@ struct GemmProb {
   double alpha;
   long long eo_off, ev_off;  // orbital energies (PK_V epilogue)
   int v, b_from_B;           // b_from_B: Bop reads the B pool (else workspace)
+  const double* pa;          // PK_GEN: A, Bop and C base pointers (offsets unused)
+  const double* pb;
+  double* pc;
+  int accumulate, pad;       // PK_GEN: 1 adds into C (atomics); 0 stores (needs ksplit 1)
 };
 
 // Per-fragment info used by the elementwise / reduction kernels.
@@ -68,8 +73,10 @@ struct FragDev {
 // ---- launchers (fp64_kernels.cu) ----
 cudaError_t launch_check_inputs(const FragDev* d_frags, int nfrag, long long max_bx,
                                 Bases bs, cudaStream_t s);
+// skip (device, may be null): when *skip != 0 at launch time every CTA returns at once
 cudaError_t launch_gemm_f64(const GemmProb* d_probs, int nprobs, long long total_tiles,
-                            Bases bs, unsigned* counter, int grid, cudaStream_t s);
+                            Bases bs, unsigned* counter, int grid, cudaStream_t s,
+                            const int* skip = nullptr);
 int gemm_f64_occupancy_grid();
 cudaError_t launch_amplitude_f64(const FragDev* d_frags, int nfrag, long long total_pairs,
                                  Bases bs, cudaStream_t s);

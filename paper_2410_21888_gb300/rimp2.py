@@ -548,3 +548,76 @@ def mlp_predict(master, feats, mean, std, stream=None) -> torch.Tensor:
     _check(_mlp_lib().rimp2_mlp_predict(_p(master), _p(feats), feats.shape[0], _p(mean), _p(std),
                                         _p(out), _stream_handle(stream)), "rimp2_mlp_predict")
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# gradient step after the densities (include/rimp2_grad.h)
+
+class ZvecArgs(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int32), ("nvir", ctypes.c_int32), ("naux", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("Bf", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("jmh", ctypes.c_void_p),
+                ("gamma", ctypes.c_void_p), ("pij", ctypes.c_void_p), ("pab", ctypes.c_void_p),
+                ("gamma_p", ctypes.c_void_p), ("lp", ctypes.c_void_p), ("lpp", ctypes.c_void_p),
+                ("dai", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+
+
+def _grad_lib():
+    lib = load()
+    if not getattr(lib, "_grad_ready", False):
+        lib.rimp2_zvec_workspace_size.argtypes = [ctypes.c_int32] * 4 + [ctypes.POINTER(ctypes.c_size_t)]
+        lib.rimp2_zvec_workspace_size.restype = ctypes.c_int
+        lib.rimp2_zvec_solve.argtypes = [ctypes.POINTER(ZvecArgs), ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]
+        lib.rimp2_zvec_solve.restype = ctypes.c_int
+        lib._grad_ready = True
+    return lib
+
+
+def _dev64(x):
+    return torch.as_tensor(x, dtype=torch.float64).to("cuda").contiguous()
+
+
+def zvector_workspace_size(nocc: int, nvir: int, naux: int, max_iter: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(_grad_lib().rimp2_zvec_workspace_size(nocc, nvir, naux, max_iter, ctypes.byref(n)),
+           "rimp2_zvec_workspace_size")
+    return n.value
+
+
+def zvector(Bf, eps, gamma, pij, pab, jmh=None, max_iter: int = 0, tol: float = 0.0,
+            workspace: torch.Tensor | None = None, stream=None, sync: bool = True) -> dict:
+    """Gamma^P, L', L'' and the Z-vector solution D_ai ([nocc][nvir]) of one fragment
+    through rimp2_zvec_solve.  Bf[n][n][naux], eps[n], gamma[nocc][nvir][naux],
+    pij[nocc][nocc], pab[nvir][nvir], jmh[naux][naux] (or None): numpy or torch, host or
+    device (copied to the device as FP64).  Returns device tensors; info = (iterations,
+    ||r|| / ||rhs||, ||rhs||)."""
+    _require_cuda()
+    lib = _grad_lib()
+    Bf_t, eps_t = _dev64(Bf), _dev64(eps)
+    g_t, pij_t, pab_t = _dev64(gamma), _dev64(pij), _dev64(pab)
+    o, v, X = (int(s) for s in g_t.shape)
+    n = o + v
+    if tuple(Bf_t.shape) != (n, n, X):
+        raise ValueError(f"Bf has shape {tuple(Bf_t.shape)}, expected {(n, n, X)}")
+    jmh_t = _dev64(jmh) if jmh is not None else None
+    f64 = dict(dtype=torch.float64, device="cuda")
+    out = {"lp": torch.empty((o, n), **f64), "lpp": torch.empty((v, n), **f64),
+           "dai": torch.empty((o, v), **f64), "info": torch.empty(3, **f64)}
+    if jmh_t is not None:
+        out["gamma_p"] = torch.empty((o, v, X), **f64)
+    need = zvector_workspace_size(o, v, X, max_iter)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+    a = ZvecArgs()
+    a.nocc, a.nvir, a.naux, a.max_iter, a.tol = o, v, X, int(max_iter), float(tol)
+    a.Bf, a.eps, a.jmh = _p(Bf_t), _p(eps_t), _p(jmh_t)
+    a.gamma, a.pij, a.pab = _p(g_t), _p(pij_t), _p(pab_t)
+    a.gamma_p = _p(out.get("gamma_p"))
+    a.lp, a.lpp, a.dai, a.info = _p(out["lp"]), _p(out["lpp"]), _p(out["dai"]), _p(out["info"])
+    _check(lib.rimp2_zvec_solve(ctypes.byref(a), _p(workspace), workspace.numel(),
+                                _stream_handle(stream)), "rimp2_zvec_solve")
+    out["_keep"] = (Bf_t, eps_t, g_t, pij_t, pab_t, jmh_t, workspace)
+    if sync:
+        torch.cuda.synchronize()
+    return out

@@ -76,11 +76,21 @@ class FullMOInputs:
 
 
 def full_mo_inputs(nocc: int, nvir: int, naux: int, seed: int = 0,
-                   sigma: float = B_SIGMA, jmh_range=(0.5, 2.0)) -> FullMOInputs:
-    """Seeded full-MO inputs around fragment_inputs(nocc, nvir, naux, seed): the
+                   sigma: float | None = None, jmh_range=(0.5, 2.0)) -> FullMOInputs:
+    """Seeded full-MO inputs around fragment_inputs(nocc, nvir, naux, seed, sigma): the
     occupied-occupied and virtual-virtual blocks of B are symmetrised normal draws of
     the same spread, J^{-1/2} = U diag(lambda) U^T with U orthogonal (QR of a normal
-    matrix) and lambda ~ U[jmh_range]."""
+    matrix) and lambda ~ U[jmh_range].
+
+    sigma defaults to 0.25 (nocc nvir naux)^(-1/4).  The Z-vector operator
+    (e_a - e_i)/2 + 2 (ai|bj) - (aj|bi) is positive definite for a stable closed-shell
+    reference, whose exchange integrals stay bounded; i.i.d. draws make the exchange
+    part's spectrum grow like sigma^2 sqrt(nocc nvir naux), and at the hot path's
+    sigma = 0.05 it already turns the operator indefinite at nocc=10, nvir=40, naux=150
+    (lowest eigenvalue -0.29).  With the default the spectrum stays within about
+    [0.25, 2.3] up to the nocc=100 nvir=500 naux=1500 fragment."""
+    if sigma is None:
+        sigma = 0.25 / max(1.0, float(nocc) * nvir * naux) ** 0.25
     frag = fragment_inputs(nocc, nvir, naux, seed, sigma)
     rng = np.random.default_rng([seed, _TAG_FULLMO])
     n = nocc + nvir

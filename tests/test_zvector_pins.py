@@ -112,3 +112,24 @@ def test_zvector_solution_satisfies_equation_by_loops():
             rhs -= sum(G(A_, i, p, q) * Dbar[p, q] for p in range(n) for q in range(n))
             worst = max(worst, abs(lhs - rhs) / (abs(rhs) + 1e-300))
     assert worst <= 1e-10
+
+
+@pytest.mark.parametrize("dims,seed", [((3, 5, 7), 4), ((5, 8, 11), 6)])
+def test_matrix_free_forms_match_dense_system(dims, seed):
+    """The matrix-free operator and right-hand side (used where the dense system does not
+    fit) against the system built from G, and single Lagrangian elements against L', L''."""
+    o, v, X = dims
+    f, ref = _inputs(o, v, X, seed)
+    A, r = zvector.zvector_system(f.Bf, f.eps, ref["gamma"], ref["pij"], ref["pab"], f.jmh, o)
+    x = np.random.default_rng(seed).normal(size=(o, v))
+    Ax = zvector.zvector_apply(f.Bf, f.eps, x, o)
+    assert np.abs(Ax.reshape(-1) - A @ x.reshape(-1)).max() <= 1e-13 * np.abs(A @ x.reshape(-1)).max()
+    rr = zvector.zvector_rhs(f.Bf, ref["gamma"], ref["pij"], ref["pab"], o)
+    assert np.abs(rr.reshape(-1) - r).max() <= 1e-12 * np.abs(r).max()
+    Lp, Lpp = zvector.lagrangian(ref["gamma"], f.Bf, f.jmh, o)
+    for (i, q) in [(0, 0), (o - 1, o + v - 1), (1, 2)]:
+        assert abs(zvector.lagrangian_elem(ref["gamma"], f.Bf, f.jmh, o, "lp", i, q) - Lp[i, q]) \
+            <= 1e-13 * np.abs(Lp).max()
+    for (a, q) in [(0, 0), (v - 1, 1), (2, o + 3)]:
+        assert abs(zvector.lagrangian_elem(ref["gamma"], f.Bf, f.jmh, o, "lpp", a, q) - Lpp[a, q]) \
+            <= 1e-13 * np.abs(Lpp).max()
