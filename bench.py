@@ -35,8 +35,8 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # (profiles/split_path_kernels_c1_dram.md), keyed by (precision, stage): 1 = V (one launch),
 # 3 = Gamma/P_ab/P_ij.  An entry is removed (traffic null) whenever its kernel changes,
 # until it is captured again.
-TRAFFIC_PER_LAUNCH = {("bf16", 3): 274_771_335_936 + 14_998_897_920,
-                      ("bf16", 1): 12_169_672_960 + 10_178_702_080}
+TRAFFIC_PER_LAUNCH = {("bf16", 3): 288_928_040_192 + 15_003_092_224,
+                      ("bf16", 1): 12_199_479_040 + 10_178_832_128}
 
 
 def flops(o, v, X):
@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage-k", type=int, default=0, choices=[0, 16, 32],
                     help="K per tensor-core pipeline stage (0: library default)")
-    ap.add_argument("--n-tile", type=int, default=0, choices=[0, 64, 80, 96])
+    ap.add_argument("--n-tile", type=int, default=0, choices=[0, 48, 64, 80, 96])
     ap.add_argument("--slices-t", type=int, default=0,
                     help="slices of the P_ab / P_ij operands; 0: precision default (6 for bf16)")
     ap.add_argument("--slices-g", type=int, default=0,

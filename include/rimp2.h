@@ -119,9 +119,12 @@ typedef struct rimp2_options {
                                  the workspace stays below this many bytes */
   int32_t stage_k;     /* split modes: K elements per pipeline stage of the tensor-core
                           GEMM, 16 or 32 (0 = default 32) */
-  int32_t n_tile;      /* BF16 split: columns per level accumulator, 64, 80 or 96, at most
-                          the widest that fits TMEM for the slice count (0 = 64: narrower
-                          tiles leave room for three pipeline stages) */
+  int32_t n_tile;      /* BF16 split: columns per level accumulator, 48, 64, 80 or 96, at
+                          most the widest that fits TMEM for the slice count (0 = 64:
+                          narrower tiles leave room for three pipeline stages).  Whenever
+                          two sets of slices x n_tile accumulator columns fit the 512 TMEM
+                          columns, the MMAs of one K chunk run while the previous chunk is
+                          drained */
   const char* autotune_cache; /* NULL, or a text file "<key> <variant>" per line: a plan
                                  whose key (precision, slices, shapes) is listed starts with
                                  that variant and skips the trials; new results are

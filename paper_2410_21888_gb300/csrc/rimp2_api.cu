@@ -451,7 +451,7 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
       (o.slices_v < 2 || o.slices_v > smax || o.slices_t < 2 || o.slices_t > smax ||
        o.slices_g < 2 || o.slices_g > smax ||
        (o.stage_k != 0 && o.stage_k != 16 && o.stage_k != 32) ||
-       (o.n_tile != 0 && o.n_tile != 64 && o.n_tile != 80 && o.n_tile != 96)))
+       (o.n_tile != 0 && o.n_tile != 48 && o.n_tile != 64 && o.n_tile != 80 && o.n_tile != 96)))
     return RIMP2_ERR_UNSUPPORTED;
   rimp2_plan* p = new (std::nothrow) rimp2_plan();
   if (!p) return RIMP2_ERR_NOMEM;

@@ -313,9 +313,9 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
   const uint32_t stage_bytes = (uint32_t)slices * (A_TILE + B_TILE);
   uint64_t* full = (uint64_t*)(smem + (size_t)stages * stage_bytes);
   uint64_t* empty = full + stages;
-  uint64_t* tmem_full = empty + stages;
-  uint64_t* tmem_empty = tmem_full + 1;
-  uint64_t* tile_full = tmem_empty + 1;      // [2]
+  uint64_t* tmem_full = empty + stages;      // [2]: one per accumulator set
+  uint64_t* tmem_empty = tmem_full + 2;      // [2]
+  uint64_t* tile_full = tmem_empty + 2;      // [2]
   uint64_t* tile_empty = tile_full + 2;      // [2]
   long long* tile_idx = (long long*)(tile_empty + 2);  // [2]
   uint32_t* tmem_base_slot = (uint32_t*)(tile_idx + 2);
@@ -327,8 +327,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(tmem_full, 1);
-    mbar_init(tmem_empty, SG_EPI_WARPS);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(tmem_full + s, 1);
+      mbar_init(tmem_empty + s, SG_EPI_WARPS);
+    }
     for (int s = 0; s < 2; ++s) {
       mbar_init(tile_full + s, 1);
       mbar_init(tile_empty + s, 1 + SG_EPI_WARPS);
@@ -348,6 +350,12 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
+  // Two sets of level accumulators when both fit the 512 TMEM columns: the MMAs of the
+  // next K chunk (or tile) then run while the epilogue warps drain the previous one.
+  // Chunk c (counted over the CTA's whole tile sequence, identically by the MMA issuer
+  // and the epilogue) uses set c % nbuf; its barrier phase is (c / nbuf) & 1.
+  const uint32_t set_cols = (uint32_t)(slices * NT);
+  const uint32_t nbuf = 2u * set_cols <= 512u ? 2u : 1u;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
@@ -404,7 +412,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       // K-major, M = 128; N (a multiple of NT up to 256) is or-ed in per MMA
       constexpr uint32_t kFmt = F8 ? 0u : 1u;   // E4M3 (kind::f8f6f4) or BF16 (kind::f16)
       const uint32_t idesc_m = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(SG_BM >> 4) << 24);
-      uint32_t st = 0, ph = 0, te_count = 0;
+      uint32_t st = 0, ph = 0, cc = 0;
       int tslot = 0;
       uint32_t tph = 0;
       for (;;) {
@@ -418,8 +426,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
         const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
         bool ok = true;
         for (int c = 0; c < chunks && ok; ++c) {
-          if (!mbar_wait(tmem_empty, (te_count & 1u) ^ 1u, abort_flag)) { ok = false; break; }
-          ++te_count;
+          const uint32_t set = cc % nbuf, use = cc / nbuf;
+          ++cc;
+          const uint32_t acc = tmem_base + set * set_cols;
+          if (!mbar_wait(tmem_empty + set, (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const int kend = min(ti.nK, (c + 1) * CHUNK_STAGES);
           for (int kk = c * CHUNK_STAGES; kk < kend; ++kk) {
@@ -428,27 +438,27 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
             const uint64_t desc = smem_desc<ROWB>(smem_u32(smem + (size_t)st * stage_bytes));
             const bool fresh = kk == c * CHUNK_STAGES;
             switch (slices) {
-              case 2: mma_stage<2, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 3: mma_stage<3, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 4: mma_stage<4, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 5: mma_stage<5, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 6: mma_stage<6, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 7: mma_stage<7, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 8: mma_stage<8, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 9: mma_stage<9, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 10: mma_stage<10, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 11: mma_stage<11, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 12: mma_stage<12, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 13: mma_stage<13, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 14: mma_stage<14, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 15: mma_stage<15, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
-              case 16: mma_stage<16, NT, ROWB, F8>(tmem_base, desc, idesc_m, fresh); break;
+              case 2: mma_stage<2, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 3: mma_stage<3, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 4: mma_stage<4, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 5: mma_stage<5, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 6: mma_stage<6, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 7: mma_stage<7, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 8: mma_stage<8, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 9: mma_stage<9, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 10: mma_stage<10, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 11: mma_stage<11, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 12: mma_stage<12, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 13: mma_stage<13, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 14: mma_stage<14, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 15: mma_stage<15, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
+              case 16: mma_stage<16, NT, ROWB, F8>(acc, desc, idesc_m, fresh); break;
               default: break;   // rejected by the host (slices in 2..16, slices * NT <= 512)
             }
             umma_commit(empty + st);   // frees this smem stage once its MMAs completed
             if (++st == (uint32_t)stages) { st = 0; ph ^= 1u; }
           }
-          if (ok) umma_commit(tmem_full);
+          if (ok) umma_commit(tmem_full + set);
         }
         if (!ok) break;
       }
@@ -461,7 +471,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
     const int c0 = (ew >> 2) * NC;             // first column of this thread
     const int row = quad * 32 + lane;          // row within the tile
     const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
-    uint32_t tf_count = 0;
+    uint32_t cc = 0;
     int tslot = 0;
     uint32_t tph = 0;
     for (;;) {
@@ -480,8 +490,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       for (int c = 0; c < NC; ++c) { acc_h[c] = 0.f; acc_l[c] = 0.f; }
       bool ok = true;
       for (int ch = 0; ch < chunks; ++ch) {
-        if (!mbar_wait(tmem_full, tf_count & 1u, abort_flag)) { ok = false; break; }
-        ++tf_count;
+        const uint32_t set = cc % nbuf, use = cc / nbuf;
+        ++cc;
+        const uint32_t set_addr = lane_addr + set * set_cols;
+        if (!mbar_wait(tmem_full + set, use & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         // Levels l < EXACT are folded into (hi, lo) by error-free sums; higher levels
         // carry at most 2^-24 of the value and are accumulated into lo directly (FMA).
@@ -489,7 +501,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
           float v[NC];
 #pragma unroll
           for (int g = 0; g < NC / 8; ++g)
-            tmem_ld8(lane_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
+            tmem_ld8(set_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
           tmem_wait_ld();
           const float sc = __int_as_float((127 - LB * l) << 23);   // 2^(-LB l)
           if (l >= EXACT) {
@@ -513,7 +525,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tmem_empty);
+        if (lane == 0) mbar_arrive(tmem_empty + set);
       }
       if (!ok) break;
       // ---------------- problem epilogue (registers only; TMEM already released)
@@ -615,9 +627,12 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   } else {
     c.bk = bk == 16 ? 16 : 32;
     // 64 columns by default: with 5 or 6 slices a stage is then small enough for three
-    // stages in shared memory, which outweighs the wider MMAs of 80- or 96-column tiles
+    // stages in shared memory, which outweighs the wider MMAs of 80- or 96-column tiles.
+    // (48 columns with 5 slices fit two accumulator sets in TMEM, 2 x 240 columns, but
+    // measured no faster on V: the drain is not what limits it.)
     const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
-    c.n_tile_max = (n_tile == 64 || n_tile == 80 || n_tile == 96) ? std::min(n_tile, widest) : 64;
+    c.n_tile_max = (n_tile == 48 || n_tile == 64 || n_tile == 80 || n_tile == 96)
+                       ? std::min(n_tile, widest) : 64;
   }
   const size_t rowb = fp8 ? 64 : (size_t)c.bk * 2;
   const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * rowb;
@@ -647,7 +662,9 @@ cudaError_t split_gemm_prepare() {
     e = cudaFuncSetAttribute(k_split_gemm<NT, ROWB, F8>,                                     \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   RIMP2_PREP(96, 64, false) RIMP2_PREP(80, 64, false) RIMP2_PREP(64, 64, false)
+  RIMP2_PREP(48, 64, false)
   RIMP2_PREP(96, 32, false) RIMP2_PREP(80, 32, false) RIMP2_PREP(64, 32, false)
+  RIMP2_PREP(48, 32, false)
   RIMP2_PREP(64, 64, true) RIMP2_PREP(48, 64, true) RIMP2_PREP(32, 64, true)
 #undef RIMP2_PREP
   return e;
@@ -666,12 +683,14 @@ cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long to
     switch (cfg.n_tile_max) {
       case 96: return launch_nt<96, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
       case 80: return launch_nt<80, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+      case 48: return launch_nt<48, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
       default: return launch_nt<64, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
     }
   }
   switch (cfg.n_tile_max) {
     case 96: return launch_nt<96, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
     case 80: return launch_nt<80, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    case 48: return launch_nt<48, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
     default: return launch_nt<64, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
 }

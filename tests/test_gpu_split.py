@@ -66,9 +66,9 @@ def _exact_levels(A, B, s, chunk=512, bits=8):
     (128, 96, 32, 5, 1),
     (200, 150, 300, 5, 2),       # ragged M/N, one chunk with a partial K block
     (256, 192, 1500, 5, 7),      # three chunks, 1500 = the large-fragment naux
-    (130, 97, 1000, 3, 3),       # two chunks
+    (130, 97, 1000, 3, 3),       # two chunks in two accumulator sets (3 x 64 columns each)
     (64, 40, 33, 4, 4),          # partial tiles and a partial K block
-    (300, 260, 700, 6, 5),       # n_tile 80
+    (300, 260, 700, 6, 5),       # six slices: one accumulator set (64-column tiles)
     (129, 70, 257, 8, 6),        # n_tile 64, eight slices
 ])
 def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
@@ -158,6 +158,15 @@ def test_split_fragment_parity(dims, seed, mode):
     else:
         out = rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", stage_k=int(mode[5:]))
     check_split(out, ref)
+
+
+@pytest.mark.parametrize("dims,seed", [((10, 40, 150), 0), ((13, 333, 150), 8)])
+def test_split_fragment_parity_48_column_tiles(dims, seed):
+    """n_tile 48: V (5 slices) then keeps two accumulator sets in TMEM (2 x 240 columns)
+    and alternates between them chunk by chunk; Gamma/P (6 slices) uses one set."""
+    f = synth.fragment_inputs(*dims, seed=seed)
+    check_split(rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", n_tile=48),
+                oracle.fragment(f.B, f.eo, f.ev))
 
 
 def test_split_degenerate_sizes():
