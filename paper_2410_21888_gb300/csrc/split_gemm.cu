@@ -240,15 +240,24 @@ struct TileInfo {
   bool skip;
 };
 
-__device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ probs, int nprobs,
-                                                long long t, int nt) {
+// Problem of work-queue entry t: binary search over the problems' first entries, in the
+// compact array `begins` when given (a few L1 lines) or else in the descriptors.
+__device__ __forceinline__ int find_problem(const SplitProb* __restrict__ probs,
+                                            const long long* __restrict__ begins, int nprobs,
+                                            long long t) {
   int lo = 0, hi = nprobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    const long long b = begins ? begins[mid] : probs[mid].tile_begin;
+    if (b <= t) lo = mid; else hi = mid - 1;
   }
+  return lo;
+}
+
+__device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ probs, int pi,
+                                                long long t, int nt) {
   TileInfo ti;
-  ti.P = probs + lo;
+  ti.P = probs + pi;
   const SplitProb* P = ti.P;
   const long long lt = t - P->tile_begin;
   const long long per = (long long)P->tiles_m * P->tiles_n;
@@ -298,8 +307,8 @@ __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm,
 // the same: ROWB bytes of K per row and pipeline stage.
 template <int NT, int ROWB, bool F8>
 __global__ void __launch_bounds__(SG_THREADS, 1)
-k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, Bases bs,
-             unsigned* __restrict__ counter, int slices, int stages) {
+k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ begins, int nprobs,
+             long long total, Bases bs, unsigned* __restrict__ counter, int slices, int stages) {
   constexpr int NC = NT / 2;                 // columns per epilogue thread
   constexpr uint32_t A_TILE = SG_BM * ROWB;  // bytes of one 128-row tile
   constexpr uint32_t B_TILE = NT * ROWB;
@@ -318,7 +327,8 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
   uint64_t* tile_full = tmem_empty + 2;      // [2]
   uint64_t* tile_empty = tile_full + 2;      // [2]
   long long* tile_idx = (long long*)(tile_empty + 2);  // [2]
-  uint32_t* tmem_base_slot = (uint32_t*)(tile_idx + 2);
+  int* tile_prob = (int*)(tile_idx + 2);               // [2]: problem of the entry (producer)
+  uint32_t* tmem_base_slot = (uint32_t*)(tile_prob + 2);
   volatile int* abort_flag = (volatile int*)(tmem_base_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -367,13 +377,17 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       uint32_t pend_ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (;;) {
         const long long t = (long long)atomicAdd(counter, 1u);
+        // the problem search is done here once per entry; the MMA and epilogue warps take
+        // its result from shared memory
+        const int pi = t < total ? find_problem(probs, begins, nprobs, t) : 0;
         if (!mbar_wait(tile_empty + tslot, tph ^ 1u, abort_flag)) break;
         tile_idx[tslot] = t;
+        tile_prob[tslot] = pi;
         mbar_arrive(tile_full + tslot);
         tslot ^= 1;
         if (tslot == 0) tph ^= 1u;
         if (t >= total) break;
-        const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+        const TileInfo ti = decode_tile(probs, pi, t, NT);
         const SplitProb* P = ti.P;
         const int rowA = ti.tm * SG_BM, rowB = ti.tn * NT;
         bool ok = true;
@@ -418,11 +432,12 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
       for (;;) {
         if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
         const long long t = tile_idx[tslot];
+        const int pi = tile_prob[tslot];
         mbar_arrive(tile_empty + tslot);
         tslot ^= 1;
         if (tslot == 0) tph ^= 1u;
         if (t >= total) break;
-        const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+        const TileInfo ti = decode_tile(probs, pi, t, NT);
         const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
         bool ok = true;
         for (int c = 0; c < chunks && ok; ++c) {
@@ -477,12 +492,13 @@ k_split_gemm(const SplitProb* __restrict__ probs, int nprobs, long long total, B
     for (;;) {
       if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
       const long long t = tile_idx[tslot];
+      const int pi = tile_prob[tslot];
       __syncwarp();
       if (lane == 0) mbar_arrive(tile_empty + tslot);
       tslot ^= 1;
       if (tslot == 0) tph ^= 1u;
       if (t >= total) break;
-      const TileInfo ti = decode_tile(probs, nprobs, t, NT);
+      const TileInfo ti = decode_tile(probs, pi, t, NT);
       if (ti.skip) continue;
       const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
       float acc_h[NC], acc_l[NC];
@@ -646,10 +662,11 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
 }
 
 template <int NT, int ROWB, bool F8>
-static cudaError_t launch_nt(const SplitProb* d_probs, int nprobs, long long total, Bases bs,
-                             unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
-  k_split_gemm<NT, ROWB, F8><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, nprobs, total, bs,
-                                                               counter, cfg.slices, cfg.stages);
+static cudaError_t launch_nt(const SplitProb* d_probs, const long long* d_begins, int nprobs,
+                             long long total, Bases bs, unsigned* counter, const SplitLaunch& cfg,
+                             int grid, cudaStream_t s) {
+  k_split_gemm<NT, ROWB, F8><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, d_begins, nprobs, total,
+                                                               bs, counter, cfg.slices, cfg.stages);
   return cudaGetLastError();
 }
 
@@ -670,28 +687,29 @@ cudaError_t split_gemm_prepare() {
   return e;
 }
 
-cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles, Bases bs,
-                              unsigned* counter, const SplitLaunch& cfg, int grid, cudaStream_t s) {
+cudaError_t launch_split_gemm(const SplitProb* d_probs, const long long* d_begins, int nprobs,
+                              long long total_tiles, Bases bs, unsigned* counter,
+                              const SplitLaunch& cfg, int grid, cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   const int g = (int)(total_tiles < grid ? total_tiles : grid);
   if (cfg.fp8) {
-    if (cfg.n_tile_max == 64) return launch_nt<64, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    if (cfg.n_tile_max == 48) return launch_nt<48, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    return launch_nt<32, 64, true>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    if (cfg.n_tile_max == 64) return launch_nt<64, 64, true>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+    if (cfg.n_tile_max == 48) return launch_nt<48, 64, true>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+    return launch_nt<32, 64, true>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
   if (cfg.bk == 32) {
     switch (cfg.n_tile_max) {
-      case 96: return launch_nt<96, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-      case 80: return launch_nt<80, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-      case 48: return launch_nt<48, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-      default: return launch_nt<64, 64, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+      case 96: return launch_nt<96, 64, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+      case 80: return launch_nt<80, 64, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+      case 48: return launch_nt<48, 64, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+      default: return launch_nt<64, 64, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
     }
   }
   switch (cfg.n_tile_max) {
-    case 96: return launch_nt<96, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    case 80: return launch_nt<80, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    case 48: return launch_nt<48, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
-    default: return launch_nt<64, 32, false>(d_probs, nprobs, total_tiles, bs, counter, cfg, g, s);
+    case 96: return launch_nt<96, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+    case 80: return launch_nt<80, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+    case 48: return launch_nt<48, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
+    default: return launch_nt<64, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
 }
 

@@ -83,9 +83,10 @@ struct SplitLaunch {
 // n_tile: columns per level accumulator (0: widest that fits 512 TMEM columns; else 64,
 // 80 or 96, capped by the TMEM budget)
 SplitLaunch split_launch_config(int slices, int bk = 32, int n_tile = 0, bool fp8 = false);
-cudaError_t launch_split_gemm(const SplitProb* d_probs, int nprobs, long long total_tiles,
-                              Bases bs, unsigned* counter, const SplitLaunch& cfg, int grid,
-                              cudaStream_t s);
+// d_begins (device, may be null): the problems' tile_begin values as a compact array
+cudaError_t launch_split_gemm(const SplitProb* d_probs, const long long* d_begins, int nprobs,
+                              long long total_tiles, Bases bs, unsigned* counter,
+                              const SplitLaunch& cfg, int grid, cudaStream_t s);
 int split_gemm_grid();
 cudaError_t split_gemm_prepare();
 

@@ -766,6 +766,9 @@ size_t split_layout_wave(SplitWave& w, size_t off) {
   w.off_pv = off; off = al256(off + w.probs_v.size() * sizeof(SplitProb));
   w.off_pc = off; off = al256(off + w.probs_c.size() * sizeof(SplitProb));
   w.off_pg = off; off = al256(off + w.probs_g.size() * sizeof(SplitProb));
+  w.off_bv = off; off = al256(off + w.probs_v.size() * sizeof(long long));
+  w.off_bc = off; off = al256(off + w.probs_c.size() * sizeof(long long));
+  w.off_bg = off; off = al256(off + w.probs_g.size() * sizeof(long long));
   return off;
 }
 
@@ -774,6 +777,15 @@ void split_fill_wave(const SplitWave& w, char* host) {
   if (!w.probs_v.empty()) memcpy(host + w.off_pv, w.probs_v.data(), w.probs_v.size() * sizeof(SplitProb));
   if (!w.probs_c.empty()) memcpy(host + w.off_pc, w.probs_c.data(), w.probs_c.size() * sizeof(SplitProb));
   if (!w.probs_g.empty()) memcpy(host + w.off_pg, w.probs_g.data(), w.probs_g.size() * sizeof(SplitProb));
+  auto begins = [&](const std::vector<SplitProb>& v, size_t off) {
+    for (size_t k = 0; k < v.size(); ++k) {
+      const long long b = v[k].tile_begin;
+      memcpy(host + off + k * sizeof(long long), &b, sizeof(b));
+    }
+  };
+  begins(w.probs_v, w.off_bv);
+  begins(w.probs_c, w.off_bc);
+  begins(w.probs_g, w.off_bg);
 }
 
 int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* dfd, int nf,
@@ -806,7 +818,8 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   }
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_v > 0) {
-    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pv), (int)w.probs_v.size(), w.tiles_v, bs,
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pv), (const long long*)(dblk + w.off_bv),
+                          (int)w.probs_v.size(), w.tiles_v, bs,
                           ctr + 0, sp.cfg_v, sp.grid, s);
     ++nl;
   }
@@ -821,12 +834,14 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   if (e == cudaSuccess) { e = launch_zero_p(dfd, nf, bs, s); ++nl; }
   if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_c > 0) {
-    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pc), (int)w.probs_c.size(), w.tiles_c, bs,
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pc), (const long long*)(dblk + w.off_bc),
+                          (int)w.probs_c.size(), w.tiles_c, bs,
                           ctr + 1, sp.cfg_t, sp.grid, s);
     ++nl;
   }
   if (e == cudaSuccess && w.tiles_g > 0) {
-    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pg), (int)w.probs_g.size(), w.tiles_g, bs,
+    e = launch_split_gemm((const SplitProb*)(dblk + w.off_pg), (const long long*)(dblk + w.off_bg),
+                          (int)w.probs_g.size(), w.tiles_g, bs,
                           ctr + 2, sp.cfg_g, sp.grid, s);
     ++nl;
   }

@@ -60,6 +60,7 @@ struct SplitWave {
   long long tiles_v = 0, tiles_c = 0, tiles_g = 0, rows = 0, b2_tiles = 0, qblks = 0;
   bool want_gamma = false;
   size_t off_sfd = 0, off_pv = 0, off_pc = 0, off_pg = 0;  // byte offsets in the device block
+  size_t off_bv = 0, off_bc = 0, off_bg = 0;  // the problems' tile_begin values (int64 each)
 };
 
 int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt);

@@ -63,7 +63,7 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
     bs.ws = (double*)buf;
     bs.gamma = C;
     bs.status = status;
-    if (launch_split_gemm((const SplitProb*)buf, 1, P.ntiles, bs, counter, cfg, split_gemm_grid(), s) !=
+    if (launch_split_gemm((const SplitProb*)buf, nullptr, 1, P.ntiles, bs, counter, cfg, split_gemm_grid(), s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       rc = RIMP2_ERR_CUDA;
