@@ -214,13 +214,15 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 
 // a / b with a correction step on the exact remainder (Dekker-style double-length
-// division): q1 = a_h / b_h, r = a - q1 b (q1 b_h formed exactly with an FMA), q2 = r / b_h.
+// division): q1 = a_h / b_h (correctly rounded), r = a - q1 b (q1 b_h formed exactly with
+// an FMA), q2 = r (1/b_h).  |q2| <= ulp(q1) / 2, so the reciprocal's ~2^-23 relative
+// error in q2 stays near 2^-47 of the quotient.
 __device__ __forceinline__ df df_div(df a, df b) {
   const float q1 = a.h / b.h;
   const float ph = q1 * b.h;
   const float pl = fmaf(q1, b.h, -ph);
   const float r = (((a.h - ph) - pl) + a.l) - q1 * b.l;
-  const float q2 = r / b.h;
+  const float q2 = r * __frcp_rn(b.h);
   return fast_two_sum(q1, q2);
 }
 
@@ -560,10 +562,13 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
           const float2* dv = (const float2*)(wsb + P->d_off);
           const float2 dm = dv[m];
           const int im = m / P->v;
+          // pair block of column n, advanced as n grows (no division per element)
+          int jn = nbase / P->v, jn_end = (jn + 1) * P->v;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const int n = nbase + c;
             if (n >= P->N) continue;
+            while (n >= jn_end) { ++jn; jn_end += P->v; }
             float s1, s2;
             pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB, s1, s2);
             df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
@@ -576,7 +581,6 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
             const df T = df_div(V, D);
             // the amplitude stage reads the pair blocks i <= j only: store (m, n) where
             // i(m) <= i(n) and the mirror (n, m) where i(n) <= i(m)
-            const int jn = n / P->v;
             if (im <= jn) {
               const long long ix = (long long)m * P->ldc + n + (long long)jn * (P->vpad - P->v);
               Th[ix] = T.h;
