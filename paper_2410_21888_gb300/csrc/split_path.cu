@@ -31,8 +31,10 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 // V tiles are walked in groups of this many rows (tile order, see decode_tile)
 constexpr int kVGroupRows = 16;
-// K extent of one Gamma slab (elements of the contracted (j,b) index)
-constexpr long long kGammaSlabK = 2048;
+// K extent of one Gamma slab (elements of the contracted (j,b) index).  Measured at
+// nocc=100 nvir=500 naux=1500 (K = 51200): the Gamma/P launch takes 144.7 ms with slabs
+// of 2048, 140.5 with 4096, 138.0 with 8192, 136.5 with 16384 and 138.5 without slabs.
+constexpr long long kGammaSlabK = 16384;
 int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
@@ -658,9 +660,11 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.tiles_m = (ov + SG_BM - 1) / SG_BM; P.tiles_n = (X + NTg - 1) / NTg;
       P.ksplit = 1; P.k0_blocks = (RL + BKg - 1) / BKg; P.k1_count = 1; P.k1_chunk = 1;
       P.a_mode = P.b_mode = TM_3D; P.div5 = 1;
-      // K = (j,b) cut into slabs of about kGammaSlabK elements, slab index outermost: the
-      // tiles in flight then share one slab, whose B digits stay in L2, and the tiles of a
-      // row start close enough together to share their Tt rows there too
+      // K = (j,b) cut into slabs of about kGammaSlabK elements (split-K for large
+      // fragments), slab index outermost: the tiles in flight share one slab, and the
+      // tiles of a row start close together, which keeps their Tt rows in L2; the slabs
+      // meet in Gamma by FP64 atomics.  Fewer, longer slabs mean fewer atomics and tile
+      // switches, which measured faster down to two or three slabs.
       const int kb = P.k0_blocks;
       int slabs = sp.variant == 3 ? 1 : (int)(((long long)kb * BKg + kGammaSlabK / 2) / kGammaSlabK);
       if (slabs > 1) {

@@ -144,7 +144,7 @@ def check_split(out, ref, tol_e=TOL_E_ABS, tol_a=TOL_A):
     ((1, 1, 1), 1),
     ((5, 31, 1), 5),
     ((4, 130, 300), 7),      # nvir > 128: several M tiles in P_ab, ragged
-    ((13, 333, 150), 8),     # Gamma's K (j,b) in two slabs, the last block past the end
+    ((13, 333, 150), 8),     # Gamma's K (j,b) with a partial last K block
 ])
 @pytest.mark.parametrize("mode", ["bf16-32", "bf16-16", "fp8", "fp8-16"])
 def test_split_fragment_parity(dims, seed, mode):
@@ -166,6 +166,14 @@ def test_split_fragment_parity_48_column_tiles(dims, seed):
     and alternates between them chunk by chunk; Gamma/P (6 slices) uses one set."""
     f = synth.fragment_inputs(*dims, seed=seed)
     check_split(rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", n_tile=48),
+                oracle.fragment(f.B, f.eo, f.ev))
+
+
+def test_split_gamma_in_two_slabs():
+    """nocc=100, nvir=250: Gamma's K = (j,b) = 100 x 256 padded elements is cut into two
+    slabs that meet in Gamma by FP64 atomics."""
+    f = synth.fragment_inputs(100, 250, 64, seed=12)
+    check_split(rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16"),
                 oracle.fragment(f.B, f.eo, f.ev))
 
 
