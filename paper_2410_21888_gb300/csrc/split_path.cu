@@ -132,18 +132,60 @@ __device__ __forceinline__ float digit_step(float& xh, float& xl) {
   return d;
 }
 
+// Two FP32 lanes in one 64-bit register for the packed f32x2 arithmetic of sm_100+
+// (add/sub/mul.rn.f32x2: each lane rounds exactly like the scalar instruction).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2x r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// digit_step on two elements at once (same operations, same rounding, per lane)
+template <int LB>
+__device__ __forceinline__ f2x digit_step2(f2x& xh, f2x& xl) {
+  const f2x kShift = f2_pack(12582912.f, 12582912.f);
+  const f2x kScale = f2_pack((float)(1 << LB), (float)(1 << LB));
+  const f2x d = f2_sub(f2_add(xh, kShift), kShift);
+  const f2x a = f2_sub(xh, d);
+  const f2x s = f2_add(a, xl);
+  const f2x e = f2_sub(xl, f2_sub(s, a));
+  xh = f2_mul(s, kScale);
+  xl = f2_mul(e, kScale);
+  return d;
+}
+
 // Digits of four consecutive elements (double-floats x[k] already scaled to the slice
-// frame), one packed store per slice plane.
+// frame), one packed store per slice plane; the digit steps run on element pairs.
 template <bool F8>
 __device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* out,
                                      long long plane) {
   constexpr int LB = Digit<F8>::LB;
   using PT = typename Pack4<F8>::T;
+  f2x h01 = f2_pack(x[0].h, x[1].h), l01 = f2_pack(x[0].l, x[1].l);
+  f2x h23 = f2_pack(x[2].h, x[3].h), l23 = f2_pack(x[2].l, x[3].l);
   for (int p = 0; p < st; ++p) {
-    const float d0 = digit_step<LB>(x[0].h, x[0].l);
-    const float d1 = digit_step<LB>(x[1].h, x[1].l);
-    const float d2 = digit_step<LB>(x[2].h, x[2].l);
-    const float d3 = digit_step<LB>(x[3].h, x[3].l);
+    float d0, d1, d2, d3;
+    f2_unpack(digit_step2<LB>(h01, l01), d0, d1);
+    f2_unpack(digit_step2<LB>(h23, l23), d2, d3);
     *(PT*)(out + p * plane) = Pack4<F8>::pack(d0, d1, d2, d3);
   }
 }
@@ -317,7 +359,9 @@ __global__ void __launch_bounds__(256, 3)
 k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   using DT = typename Digit<F8>::T;
   constexpr int LB = Digit<F8>::LB;
-  __shared__ float2 Xs[32][33], Ys[32][33];
+  // hi and lo parts of the tile pair in separate planes: with rows of 33 floats both the
+  // row-wise and the transposed reads of a warp (4 rows x 8 column groups) hit 32 banks
+  __shared__ float Xh[32][33], Xl[32][33], Yh[32][33], Yl[32][33];
   __shared__ float red_h[8], red_l[8], ros_h[8], ros_l[8];
   const int tid = threadIdx.x, r = tid >> 3, c0 = (tid & 7) * 4;
   const long long gp = blockIdx.x;
@@ -332,7 +376,7 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   char* ws = (char*)bs.ws;
   const float* Th = (const float*)(ws + F.thi);
   const float* Tl = (const float*)(ws + F.tlo);
-  const float2* dr = (const float2*)(ws + F.drow);
+  const float2* __restrict__ dr = (const float2*)(ws + F.drow);
   const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
   float s1t, s2t, s1tt, s2tt;   // 2^(LB - E) as two normal factors, for T and Tt
   pow2_factors(LB - ((int)emax - 124), s1t, s2t);
@@ -369,14 +413,19 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   auto emit = [&](const dfl t_in[4], const dfl y_in[4], long long orow, long long ocol0, int lc0,
                   bool energy, long long drow_r, long long drow_c0) {
     dfl t[4], tt[4];
+    float2 dm = make_float2(0.f, 0.f), dn[4];
+    if (energy) {   // the D terms of the row and the four columns, issued together
+      dm = dr[drow_r];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dn[k] = lc0 + k < v ? dr[drow_c0 + k] : make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const bool ok = lc0 + k < v;
       t[k] = ok ? t_in[k] : dfl{0.f, 0.f};
       tt[k] = ok ? d_add({2.f * t_in[k].h, 2.f * t_in[k].l}, d_neg(y_in[k])) : dfl{0.f, 0.f};
       if (energy && ok) {
-        const float2 dm = dr[drow_r], dn = dr[drow_c0 + k];
-        const dfl D = d_add({dm.x, dm.y}, {dn.x, dn.y});
+        const dfl D = d_add({dm.x, dm.y}, {dn[k].x, dn[k].y});
         const dfl V = d_mul(t[k], D);
         e_acc = d_add(e_acc, d_mul(tt[k], V));
         e_os = d_add(e_os, d_mul(t[k], V));
@@ -397,10 +446,10 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   if (nt > 0) load(0, 0);
   while (ta < nt) {
     __syncthreads();   // the previous pair is no longer read from shared memory
-    Xs[r][c0 + 0] = make_float2(xh.x, xl.x); Xs[r][c0 + 1] = make_float2(xh.y, xl.y);
-    Xs[r][c0 + 2] = make_float2(xh.z, xl.z); Xs[r][c0 + 3] = make_float2(xh.w, xl.w);
-    Ys[r][c0 + 0] = make_float2(yh.x, yl.x); Ys[r][c0 + 1] = make_float2(yh.y, yl.y);
-    Ys[r][c0 + 2] = make_float2(yh.z, yl.z); Ys[r][c0 + 3] = make_float2(yh.w, yl.w);
+    Xh[r][c0 + 0] = xh.x; Xh[r][c0 + 1] = xh.y; Xh[r][c0 + 2] = xh.z; Xh[r][c0 + 3] = xh.w;
+    Xl[r][c0 + 0] = xl.x; Xl[r][c0 + 1] = xl.y; Xl[r][c0 + 2] = xl.z; Xl[r][c0 + 3] = xl.w;
+    Yh[r][c0 + 0] = yh.x; Yh[r][c0 + 1] = yh.y; Yh[r][c0 + 2] = yh.z; Yh[r][c0 + 3] = yh.w;
+    Yl[r][c0 + 0] = yl.x; Yl[r][c0 + 1] = yl.y; Yl[r][c0 + 2] = yl.z; Yl[r][c0 + 3] = yl.w;
     __syncthreads();
     const int cta = ta, ctb = tb;
     if (++tb == nt) { ++ta; tb = ta; }
@@ -414,9 +463,9 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       if (la < v && lb < vpad) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float2 x = Xs[r][c0 + k], y = Ys[c0 + k][r];
-          t4[k] = tr ? dfl{y.x, y.y} : dfl{x.x, x.y};
-          y4[k] = tr ? dfl{x.x, x.y} : dfl{y.x, y.y};
+          const dfl x = {Xh[r][c0 + k], Xl[r][c0 + k]}, y = {Yh[c0 + k][r], Yl[c0 + k][r]};
+          t4[k] = tr ? y : x;
+          y4[k] = tr ? x : y;
         }
         emit(t4, y4, rowI + la, colJ + lb, lb, !tr, rowI + la, rowJ + lb);
       }
@@ -426,9 +475,9 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       if (la < v && lb < vpad) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float2 x = Ys[r][c0 + k], y = Xs[c0 + k][r];
-          t4[k] = tr ? dfl{y.x, y.y} : dfl{x.x, x.y};
-          y4[k] = tr ? dfl{x.x, x.y} : dfl{y.x, y.y};
+          const dfl x = {Yh[r][c0 + k], Yl[r][c0 + k]}, y = {Xh[c0 + k][r], Xl[c0 + k][r]};
+          t4[k] = tr ? y : x;
+          y4[k] = tr ? x : y;
         }
         emit(t4, y4, rowI + la, colJ + lb, lb, !tr, rowI + la, rowJ + lb);
       }
