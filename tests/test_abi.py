@@ -72,3 +72,31 @@ def test_binding_fails_loudly_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         rimp2.Plan([(2, 3, 4)])
+
+
+def test_zvec_host_validation_without_gpu(lib):
+    """rimp2_zvec_workspace_size and rimp2_zvec_solve check sizes, pointers and the
+    workspace before any device call."""
+    from paper_2410_21888_gb300 import rimp2
+    lib.rimp2_zvec_workspace_size.argtypes = [ctypes.c_int32] * 4 + [ctypes.POINTER(ctypes.c_size_t)]
+    lib.rimp2_zvec_solve.argtypes = [ctypes.POINTER(rimp2.ZvecArgs), ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]
+    n = ctypes.c_size_t()
+    assert lib.rimp2_zvec_workspace_size(100, 500, 1500, 0, ctypes.byref(n)) == 0
+    small = n.value
+    assert small > 100 * 100 * 1500 * 8            # holds the o*o*X exchange intermediate
+    assert lib.rimp2_zvec_workspace_size(100, 500, 1500, 200, ctypes.byref(n)) == 0
+    assert n.value > small                           # one work-queue counter per launch
+    assert lib.rimp2_zvec_workspace_size(-1, 5, 5, 0, ctypes.byref(n)) == -1
+    assert lib.rimp2_zvec_workspace_size(3, 5, 5, 0, None) == -1
+    a = rimp2.ZvecArgs()
+    a.nocc, a.nvir, a.naux = 3, 4, 5
+    assert lib.rimp2_zvec_solve(None, None, 0, None) == -1
+    assert lib.rimp2_zvec_solve(ctypes.byref(a), None, 0, None) == -1   # outputs missing
+    fake = ctypes.c_void_p(256)                      # never dereferenced: rejected first
+    a.Bf = a.eps = a.gamma = a.pij = a.pab = fake
+    a.lp = a.lpp = a.dai = a.info = fake
+    assert lib.rimp2_zvec_solve(ctypes.byref(a), None, 1 << 20, None) == -5   # no workspace
+    assert lib.rimp2_zvec_solve(ctypes.byref(a), ctypes.c_void_p(4096), 16, None) == -5
+    a.tol = -1.0
+    assert lib.rimp2_zvec_solve(ctypes.byref(a), ctypes.c_void_p(4096), 1 << 30, None) == -1
