@@ -35,8 +35,8 @@ FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp
 # (profiles/split_path_kernels_c1_dram.md), keyed by (precision, stage): 1 = V (one launch),
 # 3 = Gamma/P_ab/P_ij.  An entry is removed (traffic null) whenever its kernel changes,
 # until it is captured again.
-TRAFFIC_PER_LAUNCH = {("bf16", 3): 570_304_184_064 + 1_817_997_056,
-                      ("bf16", 1): 12_174_594_560 + 10_179_077_120}
+TRAFFIC_PER_LAUNCH = {("bf16", 3): 567_174_609_920 + 1_815_167_744,
+                      ("bf16", 1): 11_925_270_784 + 10_178_062_336}
 
 
 def flops(o, v, X):
