@@ -13,7 +13,7 @@ correction is computed (to measure the exact effect of the screen on the MBE3 to
 two rules are reported: the per-trimer rule (skip if the predicted |dE| < threshold/10)
 and the budgeted rule (skip the smallest predictions first while their predicted sum
 stays below budget/safety, by default 1e-6 Eh / 2); 5% of the skipped ones are recomputed with
-the FP64 path as the judge.  Inputs are drawn on the GPU from per-block
+the FP64 path as the audit.  Inputs are drawn on the GPU from per-block
 seeds (device_inputs).  Prints one JSON line.
 """
 from __future__ import annotations
@@ -92,9 +92,9 @@ def main():
     torch.cuda.synchronize()
     rep["predict_seconds"] = time.perf_counter() - t0
     rep["test_rmse_decades"] = float(np.sqrt(np.mean((pred.cpu().numpy() - ts.labels.cpu().numpy()) ** 2)))
-    res, _ = screen.screen_and_judge(big, sc, ts, threshold=a.threshold, margin_decades=a.margin)
+    res, _ = screen.screen_and_audit(big, sc, ts, threshold=a.threshold, margin_decades=a.margin)
     rep["threshold_rule"] = res
-    resb, _ = screen.screen_and_judge(big, sc, ts, threshold=a.threshold, margin_decades=a.margin,
+    resb, _ = screen.screen_and_audit(big, sc, ts, threshold=a.threshold, margin_decades=a.margin,
                                       budget_Eh=a.budget, safety=a.safety)
     rep["budget_rule"] = resb
     rep["budget_rule_within_1e-6_of_unscreened"] = bool(abs(resb["skipped_sum_Eh"]) <= 1e-6)

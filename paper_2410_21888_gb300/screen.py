@@ -1,7 +1,7 @@
 """Learned trimer screen: an MLP (include/rimp2_mlp.h) trained on trimer corrections
 dE_IJK that the engine itself computed predicts log10|dE_IJK| for candidate trimers;
 trimers predicted below a threshold are skipped, a random sample of the skipped ones is
-recomputed by the plain method as the judge, and the plain method stays the fallback
+recomputed by the plain method as the audit, and the plain method stays the fallback
 (screen=None).
 
 Host code here is bookkeeping (polymer lists, index tables, minibatch permutations);
@@ -228,12 +228,12 @@ def select_skips(pred_log10, threshold=1e-7, margin_decades=1.0, budget_Eh=None,
     return skip
 
 
-def screen_and_judge(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7,
-                     margin_decades=1.0, judge_fraction=0.05, seed=0, judge_precision="fp64",
+def screen_and_audit(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7,
+                     margin_decades=1.0, audit_fraction=0.05, seed=0, audit_precision="fp64",
                      budget_Eh=None, safety=10.0):
     """Applies the screen to the candidate set `ts` (whose exact corrections are known, so
     the effect on the MBE3 total is measured directly) and recomputes a random
-    `judge_fraction` of the skipped trimers with the plain method."""
+    `audit_fraction` of the skipped trimers with the plain method."""
     pred = screen.predict(ts.feats).cpu().numpy()
     skip = select_skips(pred, threshold, margin_decades, budget_Eh, safety)
     dE = ts.dE.cpu().numpy()
@@ -251,21 +251,21 @@ def screen_and_judge(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7
     res["trimer_flop_fraction_skipped"] = float(fl[skip].sum() / max(fl.sum(), 1.0))
     res["trimer_seconds_all"] = ts.trimer_seconds
     res["trimer_seconds_saved_est"] = ts.trimer_seconds * res["trimer_flop_fraction_skipped"]
-    # judge: recompute a held-out random sample of the skipped trimers with the plain method
+    # audit: recompute a held-out random sample of the skipped trimers with the plain method
     sk = np.nonzero(skip)[0]
     rng = np.random.default_rng(seed + 12345)
-    nj = int(np.ceil(judge_fraction * len(sk))) if len(sk) else 0
+    nj = int(np.ceil(audit_fraction * len(sk))) if len(sk) else 0
     if nj:
         pick = np.sort(rng.choice(sk, nj, replace=False))
-        js = trimer_set(system, None, precision=judge_precision, device_inputs=True,
-                        trimers=ts.trimers[pick]) if judge_precision == "fp64" else None
+        js = trimer_set(system, None, precision=audit_precision, device_inputs=True,
+                        trimers=ts.trimers[pick]) if audit_precision == "fp64" else None
         jd = js.dE.cpu().numpy()
-        res["judge_count"] = int(nj)
-        res["judge_max_abs_Eh"] = float(np.max(np.abs(jd)))
-        res["judge_mean_abs_Eh"] = float(np.mean(np.abs(jd)))
-        res["judge_est_skipped_abs_sum_Eh"] = float(np.mean(np.abs(jd)) * len(sk))
-        res["judge_vs_method_max_diff_Eh"] = float(np.max(np.abs(jd - dE[pick])))
-        res["judge_precision"] = judge_precision
+        res["audit_count"] = int(nj)
+        res["audit_max_abs_Eh"] = float(np.max(np.abs(jd)))
+        res["audit_mean_abs_Eh"] = float(np.mean(np.abs(jd)))
+        res["audit_est_skipped_abs_sum_Eh"] = float(np.mean(np.abs(jd)) * len(sk))
+        res["audit_vs_method_max_diff_Eh"] = float(np.max(np.abs(jd - dE[pick])))
+        res["audit_precision"] = audit_precision
     return res, skip
 
 

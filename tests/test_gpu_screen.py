@@ -2,7 +2,7 @@
 (split path with 8 slices, FP64-level), the network trained by the library's kernels,
 then candidate trimers of an unseen system screened at 1e-7 Eh.  The test shows the gain
 (trimers and trimer FLOPs skipped) and that the MBE3 total moves by at most 1e-6 Eh; a
-5% sample of the skipped trimers is recomputed by the FP64 path as the judge.
+5% sample of the skipped trimers is recomputed by the FP64 path as the audit.
 """
 import numpy as np
 import pytest
@@ -61,8 +61,8 @@ def test_screen_gain_and_error_bound():
     sc.fit(feats, labels, epochs=150, batch=256, lr=3e-3)
     assert sc.loss(feats, labels) < 0.1 * l0
     test = screen.trimer_set(_sys(20), 20.0)
-    res, skip = screen.screen_and_judge(_sys(20), sc, test, threshold=1e-7, margin_decades=1.0)
+    res, skip = screen.screen_and_audit(_sys(20), sc, test, threshold=1e-7, margin_decades=1.0)
     assert res["skipped"] > 0.2 * res["candidates"], res
     assert abs(res["skipped_sum_Eh"]) <= 1e-6, res
-    assert res["judge_count"] >= 1 and res["judge_max_abs_Eh"] < 1e-6, res
-    assert res["judge_vs_method_max_diff_Eh"] < 1e-9, res
+    assert res["audit_count"] >= 1 and res["audit_max_abs_Eh"] < 1e-6, res
+    assert res["audit_vs_method_max_diff_Eh"] < 1e-9, res
