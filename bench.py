@@ -261,9 +261,12 @@ def main():
     results = {}
     e2e_ms = e2e_h2d = e2e_clocks = None
     for prec in precs:
-        eng = rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=True,
-                           stage_k=args.stage_k, n_tile=args.n_tile,
-                           slices_t=args.slices_t, slices_g=args.slices_g)
+        def make(profile):
+            return rimp2.Engine([(o, v, X)], precision=prec, device=dev, profile_stages=profile,
+                                stage_k=args.stage_k, n_tile=args.n_tile,
+                                slices_t=args.slices_t, slices_g=args.slices_g)
+        # the timed engine records no stage events: its steps run back to back
+        eng = make(False)
         eng.set_inputs([f])
         head_run = prec == precs[0] or args.precision != "auto"
         steps = args.steps if head_run else args.fp64_steps
@@ -274,17 +277,14 @@ def main():
         eng.check_status()
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stage = [0.0, 0.0, 0.0, 0.0]
         with ClockSampler(local) as clk:
             barrier()
             e0.record(stream)
             for _ in range(steps):
                 eng.run()
-                st = eng.plan.stats()      # waits for the step; reads its stage timers
-                for k in range(4):
-                    stage[k] += st.stage_ms[k] / steps
             e1.record(stream)
             barrier()
+        eng.check_status()
         ms = e0.elapsed_time(e1) / steps
         if ws > 1:
             t = torch.tensor([ms], device=dev)
@@ -296,6 +296,21 @@ def main():
             with ClockSampler(local) as clk_e2e:
                 e2e_ms, e2e_h2d = measure_e2e(eng, f, e2e_steps, barrier)
             e2e_clocks = clk_e2e.summary()
+        # stage split from a second engine that records events between the stages (its own
+        # untimed steps: the event records and the per-step read of their times would slow
+        # the timed loop)
+        prof = make(True)
+        prof.set_inputs([f])
+        prof.run()
+        stage = [0.0, 0.0, 0.0, 0.0]
+        nprof = max(1, min(steps, 3))
+        for _ in range(nprof):
+            prof.run()
+            pst = prof.plan.stats()        # waits for the step; reads its stage timers
+            for k in range(4):
+                stage[k] += pst.stage_ms[k] / nprof
+        del prof
+        torch.cuda.empty_cache()
         results[prec] = {"ms": ms, "steps": steps, "warmup": warm, "engine": eng,
                          "clocks": clk.summary(), "launches": st.launches_per_call,
                          "energy": float(eng.energy[0].item()), "stage_ms": stage}
