@@ -133,3 +133,20 @@ def test_matrix_free_forms_match_dense_system(dims, seed):
     for (a, q) in [(0, 0), (v - 1, 1), (2, o + 3)]:
         assert abs(zvector.lagrangian_elem(ref["gamma"], f.Bf, f.jmh, o, "lpp", a, q) - Lpp[a, q]) \
             <= 1e-13 * np.abs(Lpp).max()
+
+
+@pytest.mark.parametrize("dims", [(10, 40, 150), (20, 70, 130), (30, 50, 400)])
+def test_synthetic_full_mo_inputs_keep_operator_positive_definite(dims):
+    """The size-scaled spread of synth.full_mo_inputs keeps the Z-vector operator's
+    spectrum inside ~[0.25, 2.5] (the orbital-gap range), so conjugate gradients apply;
+    the hot path's i.i.d. spread 0.05 makes it indefinite at the first of these sizes."""
+    o, v, X = dims
+    f = synth.full_mo_inputs(o, v, X, seed=1)
+    z = np.zeros((o, v, X))
+    A, _ = zvector.zvector_system(f.Bf, f.eps, z, np.zeros((o, o)), np.zeros((v, v)), f.jmh, o)
+    ev = np.linalg.eigvalsh(A)
+    assert ev.min() > 0.2 and ev.max() < 2.6, (ev.min(), ev.max())
+    if dims == (10, 40, 150):
+        g = synth.full_mo_inputs(o, v, X, seed=1, sigma=0.05)
+        A2, _ = zvector.zvector_system(g.Bf, g.eps, z, np.zeros((o, o)), np.zeros((v, v)), g.jmh, o)
+        assert np.linalg.eigvalsh(A2).min() < 0
