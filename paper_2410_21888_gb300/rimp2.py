@@ -143,7 +143,16 @@ def _stream_handle(stream) -> int:
 
 
 class Plan:
-    """rimp2_plan for a fixed list of fragment shapes (nocc, nvir, naux)."""
+    """rimp2_plan for a fixed list of fragment shapes (nocc, nvir, naux).
+
+    Options map one to one onto rimp2_options (include/rimp2.h): ``slices_v`` / ``slices_t``
+    / ``slices_g`` are the digit slices of V's operands, of P_ab / P_ij's and of Gamma's
+    (0: the precision's default; ``slices_g`` defaults to ``slices_t``); ``n_tile`` (48, 64,
+    80, 96) and ``stage_k`` (16, 32) shape the tensor-core tiles; ``profile_stages``
+    records per-stage device times (``stats().stage_ms``); ``autotune`` times the
+    contraction-stage variants in situ, optionally cached in ``autotune_cache``;
+    ``max_workspace_bytes`` splits a large batch into waves.
+    """
 
     def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 0,
                  slices_t: int = 0, use_graph: bool = True, check_inputs: bool = True,
