@@ -29,20 +29,81 @@ METRIC = "RI-MP2 energy+grad TFLOP/s and fragments/s on 1 GB300, vs plain FP64 a
 WORKLOAD = {"workload": "single fragment RI-MP2 energy+Gamma+P_ab+P_ij, nocc=100 nvir=500 "
                         "naux=1500, seed 0", "nocc": 100, "nvir": 500, "naux": 1500}
 DIMS = (100, 500, 1500)
-FP64_PEAK_TFLOPS = 1.199   # measured DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)
-# dram__bytes_read.sum + dram__bytes_write.sum of the dominant stage's launches on the
-# nocc=100 nvir=500 naux=1500 fragment from a one-pass ncu capture
-# (profiles/split_path_kernels_c1_dram.md), keyed by (precision, stage): 1 = V (one launch),
-# 3 = Gamma/P_ab/P_ij.  An entry is removed (traffic null) whenever its kernel changes,
-# until it is captured again.
-TRAFFIC_PER_LAUNCH = {("bf16", 3): 567_174_609_920 + 1_815_167_744,
-                      ("bf16", 1): 11_925_270_784 + 10_178_062_336}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel at
+# nocc=100 nvir=500 naux=1500, keyed by (precision, launch), from a one-kernel ncu capture
+# of a smaller fragment scaled to this one by the tiles processed.  An entry is removed
+# (traffic null) whenever its kernel changes, until it is captured again.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def flops(o, v, X):
     """2mnk count (V over i<=j, Gamma, P_ab, P_ij)."""
     return float(o * (o + 1) * v * v * X + 2 * o * o * v * v * X + 2 * o * o * v ** 3
                  + 2 * o ** 3 * v * v)
+
+
+def fp64_peak():
+    """FP64 throughput of this GPU measured in place by the library's test hook:
+    CUDA-core DFMA and the FP64 tensor path (mma.sync m8n8k4), TFLOP/s."""
+    import ctypes
+    from paper_2410_21888_gb300 import rimp2
+    f = rimp2.load().rimp2_testing_fp64_peak
+    f.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    out = {}
+    for kind, name in ((0, "dfma_tflops"), (1, "dmma_tflops")):
+        t = ctypes.c_double(0.0)
+        out[name] = t.value if f(kind, ctypes.byref(t)) == 0 else None
+    return out
+
+
+def oracle_golden():
+    """The oracle's full result for this fragment (seed 0), stored by
+    tests/golden/make_c1_golden.py; None when absent."""
+    p = os.path.join(ROOT, "tests", "golden", "c1_seed0.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+def mbe3_leg(seed=0, reps=3):
+    """The MBE3-shaped uneven batch: 64 monomers in a 40-bohr box (seed 0), dimers within
+    12 bohr, trimers with every pair within 10 bohr; one plan per MBE level, its launch
+    sequence captured once and replayed; inputs drawn on the device.  Split path (library
+    defaults) timed over `reps` replays, the plain FP64 path once on the same inputs."""
+    import numpy as np
+    import torch
+    from paper_2410_21888_gb300 import bench_mbe, rimp2, synth
+    system = synth.MonomerSystem(n_monomers=64, box=40.0, seed=seed)
+    rd, rt, rule = bench_mbe.CUTOFFS["stated"]
+    dimers, trimers = rimp2.mbe_polymers(system.centroids, rd, rt, rule)
+    frags, coeff = rimp2.mbe_coefficients(system.n, dimers, trimers)
+    out = {"workload": f"MBE3 batch, 64 monomers (nocc 8..20, nvir 4 nocc, naux 3 (nocc+nvir)), "
+                       f"40-bohr box, seed {seed}; dimers within {rd} bohr, trimers with every "
+                       f"pair within {rt} bohr; energy + Gamma + P_ab + P_ij per fragment",
+           "fragments": len(frags),
+           "per_level": {lvl: sum(1 for f in frags if len(f) == lvl) for lvl in (1, 2, 3)}}
+    E = {}
+    for prec, r in (("bf16", reps), ("fp64", 1)):
+        En = np.zeros(len(frags))
+        tot_ms = tot_fl = 0.0
+        for level in (1, 2, 3):
+            idx = [k for k, f in enumerate(frags) if len(f) == level]
+            if not idx:
+                continue
+            lf = [frags[k] for k in idx]
+            res, en = bench_mbe.run_level(lf, system, prec, True, 120 << 30, r, seed)
+            En[idx] = en
+            tot_ms += res["ms"]
+            tot_fl += sum(flops(*system.fragment_dims(f)) for f in lf)
+        total = rimp2.mbe_combine(torch.as_tensor(En, device="cuda"),
+                                  torch.as_tensor(coeff, dtype=torch.int32, device="cuda"))
+        E[prec] = En
+        out[prec] = {"ms": tot_ms, "fragments_per_s": len(frags) / (tot_ms * 1e-3),
+                     "tflops_fp64_equivalent": tot_fl / (tot_ms * 1e-3) / 1e12,
+                     "mbe3_energy_Eh": float(total.item()), "timed_replays": r}
+    out["max_fragment_diff_vs_fp64_path_Eh"] = float(np.max(np.abs(E["bf16"] - E["fp64"])))
+    out["mbe3_total_diff_vs_fp64_path_Eh"] = out["bf16"]["mbe3_energy_Eh"] - out["fp64"]["mbe3_energy_Eh"]
+    out["speedup_fragments_per_s"] = out["bf16"]["fragments_per_s"] / out["fp64"]["fragments_per_s"]
+    return out
 
 
 def load_peaks():
@@ -231,6 +292,8 @@ def main():
                     help="slices of the P_ab / P_ij operands; 0: precision default (6 for bf16)")
     ap.add_argument("--slices-g", type=int, default=0,
                     help="slices of the Gamma operands; 0: as --slices-t")
+    ap.add_argument("--no-mbe3", action="store_true",
+                    help="skip the MBE3 uneven-batch leg (reported under \"mbe3\")")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed steps of the plain FP64 path reported beside the split path")
     args = ap.parse_args()
@@ -303,17 +366,23 @@ def main():
         prof.set_inputs([f])
         prof.run()
         stage = [0.0, 0.0, 0.0, 0.0]
+        launch = [0.0, 0.0]
         nprof = max(1, min(steps, 3))
         for _ in range(nprof):
             prof.run()
             pst = prof.plan.stats()        # waits for the step; reads its stage timers
             for k in range(4):
                 stage[k] += pst.stage_ms[k] / nprof
+            for k in range(2):
+                launch[k] += pst.launch_ms[k] / nprof
         del prof
         torch.cuda.empty_cache()
         results[prec] = {"ms": ms, "steps": steps, "warmup": warm, "engine": eng,
                          "clocks": clk.summary(), "launches": st.launches_per_call,
-                         "energy": float(eng.energy[0].item()), "stage_ms": stage}
+                         "energy": float(eng.energy[0].item()),
+                         "energy_os": float(eng.energy_os[0].item()), "stage_ms": stage,
+                         "launch_ms": launch, "slices": list(st.slices),
+                         "tc_flops": list(st.tc_flops)}
         if not head_run:
             del eng
     if not results:
@@ -327,42 +396,59 @@ def main():
 
     peaks, peak_src = load_peaks()
     value = ws * F / (R["ms"] * 1e-3) / 1e12
-    sm = R["stage_ms"]
+    sm, lm = R["stage_ms"], R["launch_ms"]
     F_v = float(o * (o + 1) * v * v * X)
-    F_c = F - F_v
+    F_g = float(2 * o * o * v * v * X)
+    F_p = F - F_v - F_g
+    sv = stt = sg = 0
     if head == "fp64":
-        peak = FP64_PEAK_TFLOPS
+        peak = fp64_peak()
         k = 3 if sm[3] >= sm[1] else 1
-        Fk = F_c if k == 3 else F_v
+        Fk = F - F_v if k == 3 else F_v
         ach = Fk / (sm[k] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
+        roof = {"bound": "alu", "achieved": ach, "peak": peak["dfma_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peak["dfma_tflops"], "traffic": None,
                 "kernel": "k_gemm_f64 (" + ("Gamma/P_ab/P_ij" if k == 3 else "V") + ")",
-                "peak_source": "measured DFMA peak (probes/dfma_peak.cu)"}
+                "peak_source": "DFMA throughput measured in this run (rimp2_testing_fp64_peak)",
+                "fp64_peaks_tflops": peak}
     else:
         fp8 = head == "fp8"
-        sv, stt = (8, args.slices_t or 10) if fp8 else (5, args.slices_t or 6)
-        sg = args.slices_g or stt
-        prod_v, prod_t, prod_g = sv * (sv + 1) // 2, stt * (stt + 1) // 2, sg * (sg + 1) // 2
-        F_g = float(2 * o * o * v * v * X)
-        F_p = F_c - F_g
-        k = 3 if sm[3] >= sm[1] else 1
-        # stage 3: the contraction launch of Gamma, P_ab and P_ij (two launches when Gamma
-        # takes fewer slices than P)
-        Fk = F_g * prod_g + F_p * prod_t if k == 3 else F_v * prod_v
-        ach = Fk / (sm[k] * 1e-3) / 1e12
+        sv, stt, sg = R["slices"]
+        prod = {"V": sv * (sv + 1) // 2, "P": stt * (stt + 1) // 2, "G": sg * (sg + 1) // 2}
+        tc = R["tc_flops"]
+        # launches of one step: V (stage 1), the P_ab / P_ij launch (with Gamma when it has
+        # their slice count) and the separate Gamma launch (stage 3)
+        launches = {"V": (sm[1], F_v * prod["V"], tc[0], F_v, f"V, {prod['V']} slice products")}
+        if sg != stt:
+            launches["P"] = (lm[0], F_p * prod["P"], tc[1], F_p,
+                             f"P_ab/P_ij, {prod['P']} slice products")
+            launches["G"] = (lm[1], F_g * prod["G"], tc[2], F_g,
+                             f"Gamma, {prod['G']} slice products")
+        else:
+            launches["P"] = (lm[0], (F_p + F_g) * prod["P"], tc[1], F_p + F_g,
+                             f"Gamma/P_ab/P_ij, {prod['P']} slice products")
+        kname = max(launches, key=lambda n: launches[n][0])
+        t_ms, alg_fl, tc_fl, f64_fl, desc = launches[kname]
         # FP8 dense peak: the measured BF16 peak x the nominal FP8:BF16 ratio (4.5 / 2.25)
         peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if fp8 else 1.0)
+        ach = alg_fl / (t_ms * 1e-3) / 1e12
+        issued = tc_fl / (t_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get((head, k)),
-                "kernel": "k_split_gemm (" + ((f"Gamma/P_ab/P_ij, {prod_t} slice products"
-                                               if sg == stt else
-                                               f"P_ab/P_ij, {prod_t} slice products, and Gamma, "
-                                               f"{prod_g}; 2 launches") if k == 3
-                                              else f"V, {prod_v} slice products") + ")",
+                "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get((head, kname)),
+                "kernel": f"k_split_gemm ({desc})", "launch_ms": t_ms,
+                "achieved_convention": "algorithmic 2mnk FLOPs of the launch's contractions x "
+                                       "digit products / launch time",
+                "issued_tflops": issued, "issued_frac": issued / peak,
+                "issued_convention": "tensor-core FLOPs the launch issues (2 x 128 x n_tile x K "
+                                     "per computed tile, padding included, skipped symmetric "
+                                     "tiles excluded) / launch time",
                 "peak_source": f"{peak_src} bf16 dense sustained (kernel inside a long step)"
                                + (" x 2 (nominal fp8:bf16)" if fp8 else ""),
-                "fp64_equivalent_tflops": (F_c if k == 3 else F_v) / (sm[k] * 1e-3) / 1e12}
+                "fp64_equivalent_tflops": f64_fl / (t_ms * 1e-3) / 1e12,
+                "launches": {n: {"ms": l[0],
+                                 "algorithmic_tflops": l[1] / (l[0] * 1e-3) / 1e12 if l[0] > 0 else None,
+                                 "issued_tflops": l[2] / (l[0] * 1e-3) / 1e12 if l[0] > 0 else None}
+                             for n, l in launches.items()}}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": R["steps"], "warmup": R["warmup"], "ms_per_step": R["ms"],
@@ -372,6 +458,7 @@ def main():
         "config": dict(WORKLOAD, precision=head if head == "fp64" else
                        (f"{head} split, {sv} slices for V, {stt} for Gamma/P" if sg == stt else
                         f"{head} split, {sv} slices for V, {stt} for P_ab/P_ij, {sg} for Gamma"),
+                       digit_bits=None if head == "fp64" else (5 if head == "fp8" else 9),
                        l2="inputs larger than L2 (B 600 MB, workspace >> 129 MB); no flush",
                        fragments_per_s=ws * 1000.0 / R["ms"], energy_Eh=R["energy"]),
         "roofline": roof,
@@ -390,6 +477,18 @@ def main():
     }
     if "fp64" in results and head != "fp64":
         line["config"]["energy_diff_vs_fp64_path_Eh"] = R["energy"] - results["fp64"]["energy"]
+    gold = oracle_golden()
+    if gold is not None:
+        for p_, r_ in results.items():
+            line["paths"][p_]["energy_diff_vs_oracle_Eh"] = r_["energy"] - gold["energy"]
+            line["paths"][p_]["energy_os_diff_vs_oracle_Eh"] = r_["energy_os"] - gold["energy_os"]
+        line["config"]["energy_diff_vs_oracle_Eh"] = R["energy"] - gold["energy"]
+    if head != "fp64":
+        line["fp64_peaks_tflops"] = fp64_peak()
+    if rank == 0 and not args.no_mbe3 and args.precision in ("auto", "bf16"):
+        del eng, R, results
+        torch.cuda.empty_cache()
+        line["mbe3"] = mbe3_leg()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: val for k, val in cpu_baseline(f.B, f.eo, f.ev).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

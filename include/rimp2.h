@@ -21,7 +21,7 @@
  * Denominators, pair and cross-pair energy sums are FP64 in every precision mode.  In
  * RIMP2_FP64 every contraction is FP64.  In the split modes the four contractions (V,
  * Gamma, P_ab, P_ij) run on the tensor cores as sums of exact products of integer
- * digit slices (BF16: 8-bit digits; FP8 e4m3: 5-bit digits) accumulated in FP32 and
+ * digit slices (BF16: 9-bit digits; FP8 e4m3: 5-bit digits) accumulated in FP32 and
  * recombined at higher precision.
  *
  * Layouts (all row-major, element offsets into caller-owned device pools):
@@ -96,11 +96,14 @@ typedef struct rimp2_batch {
   double* energy_os; /* [nfrag] or NULL: the opposite-spin component E_OS = sum T V; the
                         same-spin one is E - E_OS (SCS-MP2, named in the paper's
                         Introduction, weights the two components) */
+  double* energy_scs; /* [nfrag] or NULL: the spin-component-scaled energy
+                         scs_os * E_OS + scs_ss * (E - E_OS), formed in FP64 from the two
+                         compensated sums, with the weights of the plan's options */
 } rimp2_batch;
 
 typedef struct rimp2_options {
   int32_t slices_v;    /* split modes: digit slices of B for V; 0 = default (BF16: 5
-                          slices of 8 bits, range 2..8; FP8: 8 slices of 5 bits, 2..16).
+                          slices of 9 bits, range 2..8; FP8: 8 slices of 5 bits, 2..16).
                           The diagonal V_ii(a,a) is taken from an FP64 row sum of
                           squares: there both operands have the same digits and the
                           truncated triangle's error would have one sign */
@@ -109,10 +112,14 @@ typedef struct rimp2_options {
                           range 2..16) */
   int32_t use_graph;   /* 1 (default): capture the launch sequence once, replay it */
   int32_t check_inputs;/* 1 (default): device check of denominators and finiteness */
-  int32_t autotune;    /* 1: the first calls of the plan each run one variant of the
-                          Gamma/P contraction stage (operand view of P_ij, split-K factor),
-                          timed in situ with CUDA events; later calls use the fastest
-                          (default 0).  Results are identical up to rounding order. */
+  int32_t autotune;    /* 1: the first calls of the plan each run one trial, timed in situ
+                          with CUDA events between the stages; later calls use the fastest
+                          (default 0).  Split modes: first one trial per tile shape (every
+                          launch - V, P_ab / P_ij, Gamma - takes its own i-th candidate of
+                          n_tile x stage_k that fits TMEM), then the other variants of the
+                          Gamma/P contraction stage (operand view of P_ij, split-K factor,
+                          Gamma slabs) with each launch's fastest shape; FP64: the split-K
+                          factor.  Results are identical up to rounding order. */
   int32_t profile_stages; /* 1: record CUDA events between the stages of each call so that
                              rimp2_get_stats reports stage_ms (default 0) */
   size_t max_workspace_bytes; /* 0: one wave for the whole batch; else waves sized so
@@ -120,22 +127,24 @@ typedef struct rimp2_options {
   int32_t stage_k;     /* split modes: K elements per pipeline stage of the tensor-core
                           GEMM, 16 or 32 (0 = default 32) */
   int32_t n_tile;      /* BF16 split: columns per level accumulator, 48, 64, 80 or 96, at
-                          most the widest that fits TMEM for the slice count (0 = 64:
-                          narrower tiles leave room for three pipeline stages).  Whenever
-                          two sets of slices x n_tile accumulator columns fit the 512 TMEM
-                          columns, the MMAs of one K chunk run while the previous chunk is
-                          drained */
+                          most the widest that fits TMEM for the slice count (0 = the
+                          widest whose two sets of slices x n_tile accumulator columns fit
+                          the 512 TMEM columns: 96, 80, 64, 48 for 2, 3, 4, 5 slices; 64
+                          for 6 or more).  With two sets the MMAs of one 128-long K chunk
+                          run while the previous chunk is drained */
   const char* autotune_cache; /* NULL, or a text file "<key> <variant>" per line: a plan
                                  whose key (precision, slices, shapes) is listed starts with
                                  that variant and skips the trials; new results are
                                  appended */
   int32_t slices_g;    /* split modes: slices of the Gamma operands: the leading slices_g
                           digit planes of Tt (one scale per fragment) and B with one scale
-                          per aux index Q; range 2..8 (BF16), 2..16 (FP8); 0 = default =
-                          slices_t, and then Gamma runs in P's launch.  Fewer slices than
-                          slices_t give a separate, cheaper Gamma launch: at the
-                          nocc=100 nvir=500 naux=1500 fragment, BF16 5 with slices_t 6
-                          measured 3.7e-10 relative Frobenius error on Gamma */
+                          per aux index Q; range 2..8 (BF16), 2..16 (FP8); 0 = default
+                          (BF16: 5, i.e. 45 bits against the per-aux-index scale of B;
+                          FP8: slices_t).  Equal to slices_t, Gamma runs in P's launch;
+                          fewer give a separate, cheaper Gamma launch */
+  double scs_os, scs_ss; /* weights of the opposite- and same-spin components in
+                            batch.energy_scs (rimp2_default_options: Grimme's SCS-MP2,
+                            6/5 and 1/3; SOS-MP2 is 1.3 and 0) */
 } rimp2_options;
 
 typedef struct rimp2_stats {
@@ -154,6 +163,20 @@ typedef struct rimp2_stats {
                               waves: [0] input checks and operand slicing, [1] V GEMM with the
                               T = V/D epilogue, [2] amplitudes, pair/total energies, zeroing,
                               [3] Gamma / P_ab / P_ij contractions */
+  int32_t slices[3];       /* split modes: digit slices in use for V, P_ab / P_ij, Gamma */
+  int32_t pad;
+  double launch_ms[2];     /* with profile_stages: stage [3] split by launch: [0] the P_ab /
+                              P_ij launch (with Gamma when it has their slice count), [1] the
+                              separate Gamma launch (0 when none) */
+  double tc_flops[4];      /* split modes: tensor-core FLOPs issued per call (2 x 128 x n_tile
+                              x K x digit products, summed over the tiles computed, padding
+                              included, skipped symmetric tiles excluded): [0] V, [1] the
+                              P_ab / P_ij launch, [2] the separate Gamma launch, [3] unused */
+  int32_t n_tile[3];       /* split modes: tile shape in use (accumulator columns, K per
+                              pipeline stage) of the V, P_ab / P_ij and Gamma launches */
+  int32_t stage_k[3];
+  int32_t tune_trials;     /* autotune: calls that run a trial (tile shapes, then variants) */
+  int32_t pad2;
 } rimp2_stats;
 
 typedef struct rimp2_plan rimp2_plan;
@@ -199,24 +222,26 @@ const char* rimp2_version(void);
 
 /* ---- no-allocation entry point (the paper has no counterpart; library plumbing) ----
  *
- * For callers that must not allocate device memory: code running where cudaMalloc is
- * forbidden or unsafe (inside a stream-ordered host callback, under an allocator that
- * owns every byte of the device, in an embedding that audits allocations).  It computes
- * the FP64 energy chain of ONE fragment - V, T = V / D, Tt, pair energies and
- * E - with the same kernels as rimp2_energy_grad, but its scratch is a file-scope
- * device array of RIMP2_NOALLOC_SCRATCH_BYTES that every GPU which loads the library
- * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * For callers that cannot allocate device memory: an allocator or framework that has
+ * reserved the whole device for itself, a latency-bound loop in which cudaMalloc's
+ * implicit synchronisation is not acceptable, a plug-in whose host audits or forbids
+ * allocations.  It computes the FP64 energy chain of ONE fragment - input checks, V,
+ * T = V / D, pair energies and E - with the kernels rimp2_energy_grad uses, but its
+ * scratch is a file-scope device array of RIMP2_NOALLOC_SCRATCH_BYTES that every GPU
+ * which loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine, and reads no host buffer after it returns.
  *
  * Arguments: B[nocc][nvir][naux] and eps[nocc + nvir] (occupied then virtual) are
  * device FP64 inputs; energy (1 double) and epair ([nocc][nocc], or NULL) are device
  * outputs, overwritten.  Asynchronous on `stream` (a cudaStream_t, NULL = legacy
  * default stream).
  *
- * Limit: 4096 + 2 * align256(8 (nocc nvir)^2) + align256(8 nocc^2) bytes must fit in
- * RIMP2_NOALLOC_SCRATCH_BYTES (about nocc * nvir <= 1440); larger fragments return
- * RIMP2_ERR_WORKSPACE before anything is launched.  Negative sizes or NULL required
- * pointers return RIMP2_ERR_BAD_ARG.
+ * Errors: the return code covers host-side checks only.  Negative sizes or NULL required
+ * pointers return RIMP2_ERR_BAD_ARG; a fragment whose scratch,
+ * 4096 + align256(8 (nocc nvir)^2) + align256(8 nocc^2) bytes, exceeds
+ * RIMP2_NOALLOC_SCRATCH_BYTES (about nocc * nvir > 2040) returns RIMP2_ERR_WORKSPACE
+ * before anything is launched.  Inputs that the device check rejects (some e_a <= e_i,
+ * or a NaN / Inf in B or eps) make *energy NaN; epair is then unspecified.
  *
  * The first call on a device looks up the array's device address (once per device,
  * with that device current) and so should come before any stream capture.  All calls

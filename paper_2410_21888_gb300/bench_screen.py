@@ -13,7 +13,10 @@ correction is computed (to measure the exact effect of the screen on the MBE3 to
 two rules are reported: the per-trimer rule (skip if the predicted |dE| < threshold/10)
 and the budgeted rule (skip the smallest predictions first while their predicted sum
 stays below budget/safety, by default 1e-6 Eh / 2); 5% of the skipped ones are recomputed with
-the FP64 path as the audit.  Inputs are drawn on the GPU from per-block
+the FP64 path as the audit.  The method without the screen, a distance cutoff, is
+compared at the same error budget: the best cutoff in hindsight on the max-pair and on
+the two-pair distance, the learned ordering with the same hindsight stop, and the exact
+ordering that bounds them all.  Inputs are drawn on the GPU from per-block
 seeds (device_inputs).  Prints one JSON line.
 """
 from __future__ import annotations
@@ -98,6 +101,18 @@ def main():
                                       budget_Eh=a.budget, safety=a.safety)
     rep["budget_rule"] = resb
     rep["budget_rule_within_1e-6_of_unscreened"] = bool(abs(resb["skipped_sum_Eh"]) <= 1e-6)
+    # the method without the screen: the best distance cutoff at the same error budget,
+    # next to the learned ordering, and the self-budgeted rule at several safety factors
+    rep["vs_distance_cutoff"] = screen.compare_with_distance_cutoff(big, ts, pred.cpu().numpy(),
+                                                                    a.budget)
+    rep["budget_rule_by_safety"] = {}
+    for sf in (1.0, 2.0, 5.0, 10.0):
+        rs, _ = screen.screen_and_audit(big, sc, ts, threshold=a.threshold,
+                                        margin_decades=a.margin, budget_Eh=a.budget, safety=sf,
+                                        audit_fraction=0.05 if sf == a.safety else 0.0)
+        rep["budget_rule_by_safety"][str(sf)] = {
+            k: rs[k] for k in ("skipped", "trimer_flop_fraction_skipped", "skipped_sum_Eh",
+                               "predicted_skipped_sum_Eh")}
     dE = np.abs(ts.dE.cpu().numpy())
     rep["exact_dE_quantiles_Eh"] = [float(x) for x in np.quantile(dE, [0.01, 0.1, 0.25, 0.5, 0.75, 0.9])]
     srt = np.sort(dE)

@@ -334,9 +334,13 @@ k_energy_reduce(const FragDev* __restrict__ frags, Bases bs) {
   };
   const double e = csum(bs.ws + F.ep_off, F.epair_off >= 0 ? bs.epair + F.epair_off : nullptr);
   if (threadIdx.x == 0) bs.energy[F.idx] = e;
-  if (bs.energy_os && F.epos_off >= 0) {
+  if ((bs.energy_os || bs.energy_scs) && F.epos_off >= 0) {
     const double eos = csum(bs.ws + F.epos_off, nullptr);
-    if (threadIdx.x == 0) bs.energy_os[F.idx] = eos;
+    if (threadIdx.x == 0) {
+      if (bs.energy_os) bs.energy_os[F.idx] = eos;
+      // spin-component scaling: c_os E_OS + c_ss E_SS with E_SS = E - E_OS
+      if (bs.energy_scs) bs.energy_scs[F.idx] = bs.scs_os * eos + bs.scs_ss * (e - eos);
+    }
   }
 }
 

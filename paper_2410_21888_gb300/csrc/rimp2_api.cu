@@ -23,6 +23,7 @@ using namespace rimp2;
 namespace {
 
 constexpr size_t kAlignElems = 32;  // 256-byte alignment of workspace regions
+constexpr int kEv = 6;               // stage events per wave
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -37,7 +38,7 @@ struct WaveDesc {
 };
 
 struct Key {
-  const void* p[9];
+  const void* p[10];
   std::vector<rimp2_frag> frags;
   bool operator==(const Key& o) const {
     if (memcmp(p, o.p, sizeof(p)) != 0 || frags.size() != o.frags.size()) return false;
@@ -72,13 +73,17 @@ struct rimp2_plan {
   bool timing_pending = false;
   rimp2_stats stats{};
   SplitPlan split;
-  std::vector<cudaEvent_t> stage_ev;   // 5 per wave when profile_stages (or autotune)
-  // autotune: 0 off, 1 trials running, 2 done
+  std::vector<cudaEvent_t> stage_ev;   // kEv per wave when profile_stages (or autotune)
+  // autotune: 0 off, 1 trials running, 2 done.  A trial is one call with one tile shape
+  // per launch (an index into the split plan's candidate lists; kBestShapes: the fastest
+  // found so far, per launch) and one contraction-stage variant.
   int tune_state = 0;
   int tune_next = 0;
-  int tune_cur = -1;                   // variant of the trial whose time is pending
+  int tune_cur = -1;                   // trial whose times are pending
   int variant = 0;                     // contraction-stage variant in use
-  double tune_ms[4] = {0, 0, 0, 0};
+  struct Trial { int shape, variant; };
+  std::vector<Trial> trials;
+  std::vector<double> tr_v, tr_p, tr_g, tr_c;   // per trial: V, P launch, Gamma launch, stage 3
   uint64_t tune_key = 0;
   std::string cache_path;
 };
@@ -106,13 +111,15 @@ const char* rimp2_status_string(int s) {
 void rimp2_default_options(rimp2_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
-  opt->slices_v = 0;   // 0: the precision's default (BF16 5 / 6, FP8 8 / 10; Gamma as P)
+  opt->slices_v = 0;   // 0: the precision's default (BF16 V 5, P 6, Gamma 5; FP8 8, 10, 10)
   opt->slices_t = 0;
   opt->slices_g = 0;
   opt->use_graph = 1;
   opt->check_inputs = 1;
   opt->autotune = 0;
   opt->max_workspace_bytes = 0;
+  opt->scs_os = 6.0 / 5.0;   // SCS-MP2 weights (Grimme)
+  opt->scs_ss = 1.0 / 3.0;
 }
 
 }  // extern "C"
@@ -268,6 +275,12 @@ int upload_descriptors(rimp2_plan* p, const rimp2_frag* frags, const double* B, 
     }
     p->waves.push_back(std::move(w));
   }
+  for (int k = 0; k < 4; ++k) p->stats.tc_flops[k] = 0.0;
+  for (const auto& w : p->waves) {
+    p->stats.tc_flops[0] += w.split.mma_v;
+    p->stats.tc_flops[1] += w.split.mma_c;
+    p->stats.tc_flops[2] += w.split.mma_g;
+  }
   // layout of the device block
   size_t off = 256;                                        // status word
   const size_t nctr = p->waves.size() * 8;
@@ -308,6 +321,7 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
   bs.B = b->B; bs.eps = b->eps; bs.ws = (double*)ws;
   bs.gamma = b->gamma; bs.pij = b->pij; bs.pab = b->pab; bs.epair = b->epair;
   bs.energy = b->energy; bs.energy_os = b->energy_os; bs.status = p->d_status;
+  bs.energy_scs = b->energy_scs; bs.scs_os = p->opt.scs_os; bs.scs_ss = p->opt.scs_ss;
   int launches = 0;
   long long tiles = 0;
   if (cudaMemsetAsync(p->d_counters, 0, p->waves.size() * 8 * sizeof(unsigned), s) != cudaSuccess)
@@ -318,7 +332,7 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
     const int nf = (int)w.fdev.size();
     unsigned* ctr = p->d_counters + wi * 8;
     cudaError_t e = cudaSuccess;
-    cudaEvent_t* ev = p->stage_ev.empty() ? nullptr : &p->stage_ev[wi * 5];
+    cudaEvent_t* ev = p->stage_ev.empty() ? nullptr : &p->stage_ev[wi * kEv];
     if (ev && cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal) != cudaSuccess) return RIMP2_ERR_CUDA;
     if (p->opt.check_inputs) {
       e = launch_check_inputs(dfd, nf, (w.max_b + 255) / 256, bs, s);
@@ -342,6 +356,7 @@ int enqueue(rimp2_plan* p, const rimp2_batch* b, void* ws, cudaStream_t s) {
       }
       tiles += w.tiles_v + w.tiles_c;
       if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
+      if (ev) cudaEventRecordWithFlags(ev[5], s, cudaEventRecordExternal);
       if (e != cudaSuccess) return RIMP2_ERR_CUDA;
     } else {
       int nl = 0;
@@ -389,36 +404,68 @@ uint64_t tune_key(const rimp2_plan* p) {
   return h;
 }
 
-int cache_lookup(const std::string& path, uint64_t key) {
-  if (path.empty()) return -1;
+constexpr int kBestShapes = -2;
+
+// A cache line is "<key> <variant> <shape V> <shape P> <shape Gamma>" (hex key; the
+// shapes are indices into the plan's candidate lists, which the options determine).
+bool cache_lookup(const std::string& path, uint64_t key, int out[4]) {
+  if (path.empty()) return false;
   FILE* fh = fopen(path.c_str(), "r");
-  if (!fh) return -1;
-  unsigned long long k = 0;
-  int v = -1, found = -1;
-  while (fscanf(fh, "%llx %d", &k, &v) == 2)
-    if (k == key) found = v;
+  if (!fh) return false;
+  char line[256];
+  bool found = false;
+  while (fgets(line, sizeof(line), fh)) {
+    unsigned long long k = 0;
+    int v[4] = {-1, 0, 0, 0};
+    if (sscanf(line, "%llx %d %d %d %d", &k, &v[0], &v[1], &v[2], &v[3]) >= 2 && k == key) {
+      for (int i = 0; i < 4; ++i) out[i] = v[i];
+      found = true;
+    }
+  }
   fclose(fh);
   return found;
 }
 
-void cache_store(const std::string& path, uint64_t key, int variant) {
+void cache_store(const std::string& path, uint64_t key, const int v[4]) {
   if (path.empty()) return;
   FILE* fh = fopen(path.c_str(), "a");
   if (!fh) return;
-  fprintf(fh, "%016llx %d\n", (unsigned long long)key, variant);
+  fprintf(fh, "%016llx %d %d %d %d\n", (unsigned long long)key, v[0], v[1], v[2], v[3]);
   fclose(fh);
 }
 
-// contraction-stage device time of the last call (events 3 -> 4 of every wave)
-double contraction_ms(rimp2_plan* p) {
+// device time between stage events a and b of the last call, summed over the waves
+double span_ms(rimp2_plan* p, int a, int b) {
   double ms = 0.0;
   for (size_t w = 0; w < p->wave_members.size(); ++w) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, p->stage_ev[w * 5 + 3], p->stage_ev[w * 5 + 4]) == cudaSuccess)
+    if (cudaEventElapsedTime(&t, p->stage_ev[w * kEv + a], p->stage_ev[w * kEv + b]) == cudaSuccess)
       ms += t;
     cudaGetLastError();
   }
   return ms;
+}
+
+void publish_shapes(rimp2_plan* p) {
+  if (p->precision == RIMP2_FP64) return;
+  const SplitLaunch* c[3] = {&p->split.cfg_v, &p->split.cfg_t, &p->split.cfg_g};
+  for (int i = 0; i < 3; ++i) {
+    p->stats.n_tile[i] = c[i]->n_tile_max;
+    p->stats.stage_k[i] = c[i]->bk;
+  }
+}
+
+// per launch, the candidate shape of the fastest shape trial
+void set_best_shapes(rimp2_plan* p) {
+  const std::vector<double>* t[3] = {&p->tr_v, &p->tr_p, &p->tr_g};
+  int best[3] = {-1, -1, -1};
+  for (int l = 0; l < 3; ++l)
+    for (size_t i = 0; i < p->trials.size(); ++i)
+      if (p->trials[i].shape >= 0 && (best[l] < 0 || (*t[l])[i] < (*t[l])[best[l]]))
+        best[l] = (int)i;
+  if (best[0] < 0) return;
+  split_set_shapes(p->split, p->trials[best[0]].shape, p->trials[best[1]].shape,
+                   p->trials[best[2]].shape);
 }
 
 double frag_flops(const rimp2_frag& f) {
@@ -445,7 +492,7 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   const bool fp8 = precision == RIMP2_FP8_SPLIT;
   if (o.slices_v == 0) o.slices_v = fp8 ? 8 : 5;
   if (o.slices_t == 0) o.slices_t = fp8 ? 10 : 6;
-  if (o.slices_g == 0) o.slices_g = o.slices_t;
+  if (o.slices_g == 0) o.slices_g = fp8 ? o.slices_t : 5;
   const int smax = fp8 ? 16 : 8;   // levels x tile width must fit the 512 TMEM columns
   if (precision != RIMP2_FP64 &&
       (o.slices_v < 2 || o.slices_v > smax || o.slices_t < 2 || o.slices_t > smax ||
@@ -482,6 +529,9 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   worst = std::max(worst, cur);
   p->ws_bytes = worst + 256;
   p->stats.waves = (int)p->wave_members.size();
+  p->stats.slices[0] = o.slices_v;
+  p->stats.slices[1] = o.slices_t;
+  p->stats.slices[2] = o.slices_g;
   double fl = 0;
   for (int f = 0; f < nfrag; ++f) fl += frag_flops(frags[f]);
   p->stats.flops_per_call = fl;
@@ -495,15 +545,34 @@ int rimp2_plan_create(const rimp2_frag* frags, int32_t nfrag, int32_t precision,
   if (o.autotune) {
     p->tune_key = tune_key(p);
     if (o.autotune_cache) p->cache_path = o.autotune_cache;
-    const int cached = cache_lookup(p->cache_path, p->tune_key);
     const int ncand = precision == RIMP2_FP64 ? kFp64Variants : kSplitVariants;
-    if (cached >= 0 && cached < ncand) { p->variant = cached; p->tune_state = 2; }
-    else p->tune_state = 1;
+    int cached[4] = {-1, 0, 0, 0};
+    if (cache_lookup(p->cache_path, p->tune_key, cached) && cached[0] >= 0 && cached[0] < ncand) {
+      p->variant = cached[0];
+      if (precision != RIMP2_FP64) split_set_shapes(p->split, cached[1], cached[2], cached[3]);
+      p->tune_state = 2;
+    } else {
+      // split paths: first one trial per tile shape (each launch takes its own i-th
+      // candidate), then the other contraction variants with each launch's fastest shape
+      if (precision == RIMP2_FP64) {
+        for (int v = 0; v < ncand; ++v) p->trials.push_back({-1, v});
+      } else {
+        const size_t ns = std::max(p->split.cand_v.size(),
+                                   std::max(p->split.cand_t.size(), p->split.cand_g.size()));
+        for (size_t i = 0; i < ns; ++i) p->trials.push_back({(int)i, 0});
+        for (int v = 1; v < ncand; ++v) p->trials.push_back({kBestShapes, v});
+      }
+      p->tr_v.assign(p->trials.size(), 0.0);
+      p->tr_p = p->tr_g = p->tr_c = p->tr_v;
+      p->tune_state = 1;
+    }
     p->stats.tune_done = p->tune_state == 2;
     p->stats.tune_variant = p->variant;
+    p->stats.tune_trials = (int)p->trials.size();
   }
+  publish_shapes(p);
   if (o.profile_stages || o.autotune) {
-    p->stage_ev.assign(p->wave_members.size() * 5, nullptr);
+    p->stage_ev.assign(p->wave_members.size() * kEv, nullptr);
     for (auto& e : p->stage_ev)
       if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); rimp2_plan_destroy(p); return RIMP2_ERR_CUDA; }
   }
@@ -551,34 +620,63 @@ int rimp2_energy_grad(rimp2_plan* p, const rimp2_batch* b, void* workspace, size
   cudaStream_t s = (cudaStream_t)stream;
 
   if (p->tune_state == 1) {
-    // in-situ trials: the time of the previous call's variant, then the next variant
-    const int ncand = p->precision == RIMP2_FP64 ? kFp64Variants : kSplitVariants;
+    // in-situ trials (the paper's runtime GEMM variant selection): read the times of the
+    // previous call's trial, then set up the next trial or, after the last one, the
+    // fastest shapes and variant
     if (p->tune_cur >= 0) {
       if (cudaEventSynchronize(p->done) != cudaSuccess) return RIMP2_ERR_CUDA;
-      p->tune_ms[p->tune_cur] = contraction_ms(p);
-      p->stats.tune_ms[p->tune_cur] = p->tune_ms[p->tune_cur];
+      const int t = p->tune_cur;
+      p->tr_v[t] = span_ms(p, 1, 2);
+      p->tr_p[t] = span_ms(p, 3, 4);
+      p->tr_g[t] = span_ms(p, 4, 5);
+      p->tr_c[t] = span_ms(p, 3, 5);
+      if (p->trials[t].variant < 4) p->stats.tune_ms[p->trials[t].variant] = p->tr_c[t];
       p->tune_cur = -1;
     }
-    int next = -1;
-    if (p->tune_next < ncand) next = p->tune_next++;
-    else {
-      next = 0;
-      for (int v = 1; v < ncand; ++v)
-        if (p->tune_ms[v] < p->tune_ms[next]) next = v;
+    const bool split = p->precision != RIMP2_FP64;
+    if (p->tune_next < (int)p->trials.size()) {
+      const int t = p->tune_next++;
+      const auto tr = p->trials[t];
+      if (split && tr.shape >= 0) split_set_shapes(p->split, tr.shape, tr.shape, tr.shape);
+      if (split && tr.shape == kBestShapes) set_best_shapes(p);
+      p->variant = tr.variant;
+      p->tune_cur = t;
+      p->have_desc = false;   // rebuild descriptors and graph for this trial
+    } else {
+      int best = -1;
+      double best_ms = 0.0;
+      if (split) {
+        set_best_shapes(p);
+        // variant 0 with the fastest shapes: the sum of the two launches' best times
+        double v0p = -1.0, v0g = -1.0;
+        for (size_t i = 0; i < p->trials.size(); ++i)
+          if (p->trials[i].shape >= 0) {
+            if (v0p < 0 || p->tr_p[i] < v0p) v0p = p->tr_p[i];
+            if (v0g < 0 || p->tr_g[i] < v0g) v0g = p->tr_g[i];
+          }
+        best = 0;
+        best_ms = v0p + v0g;
+        p->stats.tune_ms[0] = best_ms;
+      }
+      for (size_t i = 0; i < p->trials.size(); ++i)
+        if (!(split && p->trials[i].shape >= 0) && (best < 0 || p->tr_c[i] < best_ms)) {
+          best = p->trials[i].variant;
+          best_ms = p->tr_c[i];
+        }
+      p->variant = best;
       p->tune_state = 2;
       p->stats.tune_done = 1;
-      cache_store(p->cache_path, p->tune_key, next);
+      const int rec[4] = {best, p->split.shape_v, p->split.shape_t, p->split.shape_g};
+      cache_store(p->cache_path, p->tune_key, rec);
+      p->have_desc = false;
     }
-    if (next != p->variant || !p->have_desc) {
-      p->variant = next;
-      p->have_desc = false;   // rebuild descriptors and graph for this variant
-    }
-    if (p->tune_state == 1) p->tune_cur = next;
     p->stats.tune_variant = p->variant;
+    publish_shapes(p);
   }
   Key k{};
   k.p[0] = b->B; k.p[1] = b->eps; k.p[2] = workspace; k.p[3] = b->gamma; k.p[4] = b->pij;
   k.p[5] = b->pab; k.p[6] = b->epair; k.p[7] = b->energy; k.p[8] = b->energy_os;
+  k.p[9] = b->energy_scs;
   k.frags.assign(b->frags, b->frags + b->nfrag);
   const bool changed = !p->have_desc || !(k == p->key);
   if (changed) {
@@ -655,13 +753,22 @@ int rimp2_get_stats(rimp2_plan* p, rimp2_stats* out) {
   if (!p->stage_ev.empty() && p->stats.calls > 0) {
     if (cudaEventSynchronize(p->done) != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
     for (int k = 0; k < 4; ++k) p->stats.stage_ms[k] = 0.0;
-    for (size_t w = 0; w < p->wave_members.size(); ++w)
-      for (int k = 0; k < 4; ++k) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p->stage_ev[w * 5 + k], p->stage_ev[w * 5 + k + 1]) == cudaSuccess)
-          p->stats.stage_ms[k] += ms;
-        cudaGetLastError();
-      }
+    p->stats.launch_ms[0] = p->stats.launch_ms[1] = 0.0;
+    // events per wave: start, after slicing, after V, after the amplitude stage, after
+    // the P_ab / P_ij (and Gamma) launch, after the separate Gamma launch
+    auto span = [&](size_t w, int a, int b) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p->stage_ev[w * kEv + a], p->stage_ev[w * kEv + b]) != cudaSuccess)
+        ms = 0.f;
+      cudaGetLastError();
+      return (double)ms;
+    };
+    for (size_t w = 0; w < p->wave_members.size(); ++w) {
+      for (int k = 0; k < 3; ++k) p->stats.stage_ms[k] += span(w, k, k + 1);
+      p->stats.stage_ms[3] += span(w, 3, 5);
+      p->stats.launch_ms[0] += span(w, 3, 4);
+      p->stats.launch_ms[1] += span(w, 4, 5);
+    }
   }
   *out = p->stats;
   return RIMP2_OK;

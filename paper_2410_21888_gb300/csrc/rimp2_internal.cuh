@@ -38,6 +38,8 @@ struct Bases {
   double* epair;
   double* energy;
   double* energy_os;   // may be null
+  double* energy_scs;  // may be null: scs_os * E_OS + scs_ss * (E - E_OS)
+  double scs_os, scs_ss;
   unsigned* status;
 };
 

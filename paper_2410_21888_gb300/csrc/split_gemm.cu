@@ -6,8 +6,10 @@
 // the 512 TMEM columns).
 //
 // Every mbarrier wait is bounded (globaltimer, 2 s): on expiry the CTA records
-// ST_TIMEOUT in the status word, stops all roles, waits (bounded) for its own TMA
-// loads in flight, frees its TMEM and returns.
+// ST_TIMEOUT in the status word and stops all roles; the MMA issuer commits the MMAs it
+// has issued to an mbarrier and waits for them, the TMA producer waits for its own loads
+// in flight (both bounded by the normal limit), and only then is TMEM freed and the CTA
+// returns.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -48,6 +50,19 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* b, uint32_t parity) 
   return ok;
 }
 
+// non-blocking probe of the same phase
+__device__ __forceinline__ uint32_t mbar_test_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -56,9 +71,20 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a healthy wait takes microseconds
 
-// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+// Limit of the consumer-side waits (the MMA issuer and the epilogue warps).  A test hook
+// (rimp2_testing_set_wait_limit) shortens it so that those waits expire on purpose; the
+// producer's waits and the drains after an abort always keep kWaitLimitNs.
+__device__ unsigned long long g_sg_consumer_wait_ns = kWaitLimitNs;
+
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.  A limit of 0
+// (test hook) gives up unless one non-blocking probe finds the phase complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
                                           uint64_t limit_ns = kWaitLimitNs) {
+  if (limit_ns == 0) {
+    if (mbar_test_wait(b, parity)) return true;
+    *abort_flag = 1;
+    return false;
+  }
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
@@ -67,6 +93,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
       if (*abort_flag) return false;
       if (global_ns() - t0 > limit_ns) {
         *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// The same wait for a whole warp whose lanes all call it: the lanes leave together, on
+// success once every lane has seen the phase complete (it stays complete until this warp
+// arrives on the paired barrier), on timeout or abort by lane 0's decision, so that no
+// lane runs ahead into a .sync.aligned tcgen05 instruction without the others.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity,
+                                               volatile int* abort_flag, uint64_t limit_ns) {
+  const bool lead = (threadIdx.x & 31) == 0;
+  if (limit_ns == 0) {   // uniform across the warp
+    if (__all_sync(0xffffffffu, mbar_test_wait(b, parity))) return true;
+    if (lead) *abort_flag = 1;
+    __syncwarp();
+    return false;
+  }
+  const uint64_t t0 = lead ? global_ns() : 0;
+  for (uint32_t it = 1;; ++it) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(b, parity))) return true;
+    if ((it & 63u) == 0) {
+      int give_up = 0;
+      if (lead) give_up = (*abort_flag != 0) || (global_ns() - t0 > limit_ns);
+      if (__shfl_sync(0xffffffffu, give_up, 0)) {
+        if (lead) *abort_flag = 1;
+        __syncwarp();
         return false;
       }
     }
@@ -214,17 +268,28 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return fast_two_sum(s.h, s.l);
 }
 
-// a / b with a correction step on the exact remainder (Dekker-style double-length
-// division): q1 = a_h / b_h (correctly rounded), r = a - q1 b (q1 b_h formed exactly with
-// an FMA), q2 = r (1/b_h).  |q2| <= ulp(q1) / 2, so the reciprocal's ~2^-23 relative
-// error in q2 stays near 2^-47 of the quotient.
+// a / b in double-float: q1 = a_h / b_h (correctly rounded), then two correction terms
+// from the remainders, q2 = (a - q1 b) / b_h and q3 = (a - q1 b - q2 b) / b_h, each
+// remainder formed with the exact product error of q b_h (FMA) and the b_l term, and the
+// division by b_h done with its correctly rounded reciprocal.  One correction term alone
+// leaves q2's error, whose part (b_l / b_h) (a - q1 b) / b_h is correlated with q2 and
+// biases |T| low by ~6e-16 relative (measured by exact rational arithmetic on 4e4
+// quotients), i.e. ~1e-15 of the energy; the third term removes it (mean error below
+// 2e-17, rms 1.6e-15).  The products are written with __fmul_rn so that the compiler
+// cannot contract them into the additions of the error-free transformations.
 __device__ __forceinline__ df df_div(df a, df b) {
-  const float q1 = a.h / b.h;
-  const float ph = q1 * b.h;
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const float rc = __frcp_rn(b.h);
+  const float ph = __fmul_rn(q1, b.h);
   const float pl = fmaf(q1, b.h, -ph);
-  const float r = (((a.h - ph) - pl) + a.l) - q1 * b.l;
-  const float q2 = r * __frcp_rn(b.h);
-  return fast_two_sum(q1, q2);
+  const float r = fmaf(-q1, b.l, __fadd_rn(__fsub_rn(__fsub_rn(a.h, ph), pl), a.l));
+  const float q2 = __fmul_rn(r, rc);
+  const float ph2 = __fmul_rn(q2, b.h);
+  const float pl2 = fmaf(q2, b.h, -ph2);
+  const float r2 = fmaf(-q2, b.l, __fsub_rn(__fsub_rn(r, ph2), pl2));
+  const float q3 = __fmul_rn(r2, rc);
+  const df s = fast_two_sum(q1, q2);
+  return fast_two_sum(s.h, __fadd_rn(s.l, q3));
 }
 
 // 2^e as float for e in [-252, 254] via two normal factors
@@ -316,9 +381,12 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
   constexpr uint32_t A_TILE = SG_BM * ROWB;  // bytes of one 128-row tile
   constexpr uint32_t B_TILE = NT * ROWB;
   constexpr int BKE = F8 ? ROWB : ROWB / 2;  // K elements per stage
-  constexpr int CHUNK_STAGES = SG_CHUNK_K / BKE;
-  constexpr int LB = F8 ? 5 : 8;             // bits per digit
-  constexpr int EXACT = F8 ? 5 : 3;          // levels folded by error-free sums (LB*l < 24)
+  constexpr int CHUNK_STAGES = (F8 ? SG_CHUNK_K_FP8 : SG_CHUNK_K_BF16) / BKE;
+  constexpr int LB = F8 ? SG_LB_FP8 : SG_LB_BF16;   // bits per digit
+  // Levels l < EXACT are folded into the (hi, lo) accumulator by error-free sums (the
+  // integer levels and, for BF16, level 2, whose FP32 sums can reach 2^24); the higher
+  // levels carry at most 2^-24 of the value and are added into lo by an FMA.
+  constexpr int EXACT = F8 ? 5 : 3;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -329,7 +397,8 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
   uint64_t* tmem_empty = tmem_full + 2;      // [2]
   uint64_t* tile_full = tmem_empty + 2;      // [2]
   uint64_t* tile_empty = tile_full + 2;      // [2]
-  long long* tile_idx = (long long*)(tile_empty + 2);  // [2]
+  uint64_t* mma_drain = tile_empty + 2;      // [1]: MMAs in flight at an abort
+  long long* tile_idx = (long long*)(mma_drain + 1);   // [2]
   int* tile_prob = (int*)(tile_idx + 2);               // [2]: problem of the entry (producer)
   uint32_t* tmem_base_slot = (uint32_t*)(tile_prob + 2);
   volatile int* abort_flag = (volatile int*)(tmem_base_slot + 1);
@@ -348,6 +417,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
       mbar_init(tile_full + s, 1);
       mbar_init(tile_empty + s, 1 + SG_EPI_WARPS);
     }
+    mbar_init(mma_drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -363,6 +433,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_base_slot;
+  const uint64_t cwait = g_sg_consumer_wait_ns;   // consumer-side wait limit
   // Two sets of level accumulators when both fit the 512 TMEM columns: the MMAs of the
   // next K chunk (or tile) then run while the epilogue warps drain the previous one.
   // Chunk c (counted over the CTA's whole tile sequence, identically by the MMA issuer
@@ -417,7 +488,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         for (int s = 0; s < stages && s < 8; ++s)
           if (pending[s]) {
             const uint64_t t0 = global_ns();
-            while (!mbar_try_wait(full + s, pend_ph[s]) && global_ns() - t0 < 100000000ull) { }
+            while (!mbar_try_wait(full + s, pend_ph[s]) && global_ns() - t0 < kWaitLimitNs) { }
           }
       }
     }
@@ -433,7 +504,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
       int tslot = 0;
       uint32_t tph = 0;
       for (;;) {
-        if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
+        if (!mbar_wait(tile_full + tslot, tph, abort_flag, cwait)) break;
         const long long t = tile_idx[tslot];
         const int pi = tile_prob[tslot];
         mbar_arrive(tile_empty + tslot);
@@ -447,11 +518,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
           const uint32_t set = cc % nbuf, use = cc / nbuf;
           ++cc;
           const uint32_t acc = tmem_base + set * set_cols;
-          if (!mbar_wait(tmem_empty + set, (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(tmem_empty + set, (use & 1u) ^ 1u, abort_flag, cwait)) { ok = false; break; }
           tc_fence_after();
           const int kend = min(ti.nK, (c + 1) * CHUNK_STAGES);
           for (int kk = c * CHUNK_STAGES; kk < kend; ++kk) {
-            if (!mbar_wait(full + st, ph, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(full + st, ph, abort_flag, cwait)) { ok = false; break; }
             tc_fence_after();
             const uint64_t desc = smem_desc<ROWB>(smem_u32(smem + (size_t)st * stage_bytes));
             const bool fresh = kk == c * CHUNK_STAGES;
@@ -480,6 +551,14 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         }
         if (!ok) break;
       }
+      if (*abort_flag) {
+        // MMAs issued before the abort may still read shared memory and write TMEM:
+        // commit them to an mbarrier and wait (bounded by the normal limit, whatever
+        // the abort flag says) before the teardown frees TMEM
+        umma_commit(mma_drain);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(mma_drain, 0) && global_ns() - t0 < kWaitLimitNs) { }
+      }
     }
     __syncwarp();
   } else {
@@ -493,7 +572,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
     int tslot = 0;
     uint32_t tph = 0;
     for (;;) {
-      if (!mbar_wait(tile_full + tslot, tph, abort_flag)) break;
+      if (!mbar_wait_warp(tile_full + tslot, tph, abort_flag, cwait)) break;
       const long long t = tile_idx[tslot];
       const int pi = tile_prob[tslot];
       __syncwarp();
@@ -512,10 +591,8 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         const uint32_t set = cc % nbuf, use = cc / nbuf;
         ++cc;
         const uint32_t set_addr = lane_addr + set * set_cols;
-        if (!mbar_wait(tmem_full + set, use & 1u, abort_flag)) { ok = false; break; }
+        if (!mbar_wait_warp(tmem_full + set, use & 1u, abort_flag, cwait)) { ok = false; break; }
         tc_fence_after();
-        // Levels l < EXACT are folded into (hi, lo) by error-free sums; higher levels
-        // carry at most 2^-24 of the value and are accumulated into lo directly (FMA).
         for (int l = slices - 1; l >= 0; --l) {
           float v[NC];
 #pragma unroll
@@ -644,13 +721,14 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   c.fp8 = fp8;
   if (fp8) {
     c.bk = 64;                       // 64 one-byte elements per 64-byte row
-    c.n_tile_max = slices <= 8 ? 64 : (slices <= 10 ? 48 : 32);
+    c.n_tile_max = (n_tile == 32 || n_tile == 48 || n_tile == 64) && slices * n_tile <= 512
+                       ? n_tile : (slices <= 8 ? 64 : (slices <= 10 ? 48 : 32));
   } else {
     c.bk = bk == 16 ? 16 : 32;
     // 64 columns by default: with 5 or 6 slices a stage is then small enough for three
     // stages in shared memory, which outweighs the wider MMAs of 80- or 96-column tiles.
     // (48 columns with 5 slices fit two accumulator sets in TMEM, 2 x 240 columns, but
-    // measured no faster on V: the drain is not what limits it.)
+    // measured no faster: with 512-long chunks the drain is not what limits the kernel.)
     const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
     c.n_tile_max = (n_tile == 48 || n_tile == 64 || n_tile == 80 || n_tile == 96)
                        ? std::min(n_tile, widest) : 64;
@@ -716,6 +794,11 @@ cudaError_t launch_split_gemm(const SplitProb* d_probs, const long long* d_begin
     case 48: return launch_nt<48, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
     default: return launch_nt<64, 32, false>(d_probs, d_begins, nprobs, total_tiles, bs, counter, cfg, g, s);
   }
+}
+
+cudaError_t split_gemm_set_consumer_wait(long long ns) {
+  const unsigned long long v = ns < 0 ? kWaitLimitNs : (unsigned long long)ns;
+  return cudaMemcpyToSymbol(g_sg_consumer_wait_ns, &v, sizeof(v));
 }
 
 int split_gemm_grid() {

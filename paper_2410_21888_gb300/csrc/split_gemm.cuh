@@ -1,18 +1,21 @@
 // Split-precision tensor-core GEMM (tcgen05, sm_103a): shared declarations.
 //
-// Operands are "slices": balanced base-256 integer digits d_p in [-128, 128] of FP64
-// values relative to a power-of-two scale, stored as BF16 (exact for such integers):
-//   x ~= sum_p d_p 2^(E - 8(p+1)),   |x| < 2^(E-1),
-// or (FP8 mode) balanced base-32 digits in [-16, 16] stored as e4m3 (exact), with 5 in
-// place of 8 in every formula below; then |digit product| <= 2^8 and every level sum of
-// a 512-long chunk is an exact integer.
-// C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 16) sum_l 2^(-8 l) S_l with
+// Operands are "slices": balanced base-512 integer digits of FP64 values relative to a
+// power-of-two scale, stored as BF16 (its 8-bit significand holds every integer up to
+// 256 exactly):
+//   x ~= sum_p d_p 2^(E - 9(p+1)),   |x| <= 2^(E-3),
+// so that the leading digit d_0 lies in [-64, 64] and the others in [-256, 256]; or (FP8
+// mode) balanced base-32 digits in [-16, 16] stored as e4m3 (exact), |x| <= 2^(E-1),
+// with 5 in place of 9 in every formula below.
+// C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 2 LB) sum_l 2^(-LB l) S_l with
 // S_l = sum_{p+q=l} sum_k dA_p dB_q, the truncated level sum kept for l < s.  Each S_l
-// accumulates in its own FP32 TMEM accumulator over K chunks of 512, where levels 0
-// and 1 are exact integers by construction (|S_l| <= 2 * 512 * 2^14 = 2^24); a level
+// accumulates in its own FP32 TMEM accumulator over K chunks of 512, where levels 0 and
+// 1 are exact integers by construction (BF16: |S_0| <= 512 * 2^12 = 2^21 and
+// |S_1| <= 512 * 2 * 2^6 * 2^8 = 2^24, the narrow leading digit is what allows 512;
+// FP8: every level of up to 16 slices stays below 16 * 512 * 2^8 < 2^24); a BF16 level
 // l >= 2 rounds only if its partial sum exceeds 2^24 in magnitude, which bounds that
-// error by 2^-24 of the level, i.e. 2^-40 of the level sums' magnitude.  Each chunk is
-// then folded into a per-element double-float (hi, lo) accumulator in registers.
+// error by 2^-24 of the level.  Each chunk is then folded into a per-element
+// double-float (hi, lo) accumulator in registers.
 #pragma once
 
 #include <cuda.h>
@@ -25,7 +28,11 @@ namespace rimp2 {
 
 constexpr int SG_BM = 128;          // rows per tile (TMEM lanes)
 constexpr int SG_BN_MAX = 96;       // max columns per tile
-constexpr int SG_CHUNK_K = 512;     // K elements per accumulation chunk
+// bits per digit, K elements per accumulation chunk, and the bits by which the leading
+// digit is narrower than the others (the scale of x is 2^E with |x| <= 2^(E-1-HEAD)), of
+// each digit format
+constexpr int SG_LB_BF16 = 9, SG_CHUNK_K_BF16 = 512, SG_HEAD_BF16 = 2;
+constexpr int SG_LB_FP8 = 5, SG_CHUNK_K_FP8 = 512, SG_HEAD_FP8 = 0;
 // K per pipeline stage: 32 (64-byte rows, 64B swizzle) or 16 (32-byte rows, 32B swizzle);
 // the smaller stage fits twice as many stages in shared memory
 constexpr int SG_MAX_SLICES = 16;   // FP8; BF16 stops at 8
@@ -88,6 +95,9 @@ cudaError_t launch_split_gemm(const SplitProb* d_probs, const long long* d_begin
                               long long total_tiles, Bases bs, unsigned* counter,
                               const SplitLaunch& cfg, int grid, cudaStream_t s);
 int split_gemm_grid();
+// Consumer-side wait limit of the contraction kernel on the current device (ns < 0: the
+// normal 2 s); synchronous.  Used by a test hook only.
+cudaError_t split_gemm_set_consumer_wait(long long ns);
 cudaError_t split_gemm_prepare();
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)

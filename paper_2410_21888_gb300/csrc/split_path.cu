@@ -58,8 +58,9 @@ __device__ __forceinline__ dfl d_add(dfl a, dfl b) {
   return d_fast(s.h, s.l);
 }
 __device__ __forceinline__ dfl d_neg(dfl a) { return {-a.h, -a.l}; }
+// (__fmul_rn: the rounded product must not be contracted into d_fast's addition)
 __device__ __forceinline__ dfl d_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
+  const float p = __fmul_rn(a.h, b.h);
   float e = fmaf(a.h, b.h, -p);
   e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
   return d_fast(p, e);
@@ -81,17 +82,22 @@ __device__ __forceinline__ int find_sfd(const SplitFragDev* __restrict__ f, int 
   return lo;
 }
 
-// One digit (an integer in [-2^(LB-1), 2^(LB-1)]) in the slice format: BF16 (LB = 8)
-// or FP8 e4m3 (LB = 5); both represent these integers exactly.
+// One digit (an integer in [-2^(LB-1), 2^(LB-1)]) in the slice format: BF16 (LB = 9:
+// its 8-bit significand holds every integer up to 256) or FP8 e4m3 (LB = 5); both
+// represent these integers exactly.  The leading digit is HEAD bits narrower: a value x
+// is sliced relative to 2^E with |x| <= 2^(E-1-HEAD) (BF16: d_0 in [-64, 64], which keeps
+// the level-1 sums of a 512-long chunk within 2^24).
 template <bool F8> struct Digit;
 template <> struct Digit<false> {
   using T = __nv_bfloat16;
-  static constexpr int LB = 8;
+  static constexpr int LB = SG_LB_BF16;
+  static constexpr int HEAD = SG_HEAD_BF16;
   __device__ static T enc(float d) { return __float2bfloat16_rn(d); }
 };
 template <> struct Digit<true> {
   using T = unsigned char;
-  static constexpr int LB = 5;
+  static constexpr int LB = SG_LB_FP8;
+  static constexpr int HEAD = SG_HEAD_FP8;
   __device__ static T enc(float d) {
     return (T)__nv_cvt_float_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
   }
@@ -250,7 +256,7 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     ss += __shfl_xor_sync(0xffffffffu, ss, off);
   }
-  const int E = mx > 0.0 ? ilogb(mx) + 2 : -1000;
+  const int E = mx > 0.0 ? ilogb(mx) + 2 + Digit<F8>::HEAD : -1000;
   char* ws = (char*)bs.ws;
   const long long plane = (long long)F.o * F.v * F.xpad;
   DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
@@ -298,7 +304,7 @@ k_bcol_max(const SplitFragDev* __restrict__ f, int nf, Bases bs) {
 }
 
 // Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale
-// 2^E_Q per aux index, E_Q = ilogb(max_(j,b) |B^Q_jb|) + 2 (also stored for the GEMM
+// 2^E_Q per aux index, E_Q = ilogb(max_(j,b) |B^Q_jb|) + 2 + HEAD (also stored for the GEMM
 // epilogue).  32 x 32 tiles transposed through shared memory.
 template <bool F8>
 __global__ void __launch_bounds__(256)
@@ -332,7 +338,7 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
     const int Q = tq * 32 + r, c = tc * 32 + tx;
     if (Q >= F.X) continue;
     const double mq = __longlong_as_double((long long)cm[Q]);
-    const int E = mq > 0.0 ? ilogb(mq) + 2 : -1000;
+    const int E = mq > 0.0 ? ilogb(mq) + 2 + Digit<F8>::HEAD : -1000;
     if (tc == 0 && tx == 0) ec[Q] = E;
     if (c < RL) {
       float s1, s2;
@@ -379,8 +385,11 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const float2* __restrict__ dr = (const float2*)(ws + F.drow);
   const unsigned emax = *(const unsigned*)(ws + F.scal + 4);
   float s1t, s2t, s1tt, s2tt;   // 2^(LB - E) as two normal factors, for T and Tt
-  pow2_factors(LB - ((int)emax - 124), s1t, s2t);
-  pow2_factors(LB - ((int)emax - 123), s1tt, s2tt);
+  // |T| < 2^(emax - 126) and |Tt| <= 3 max |T| < 2^(emax - 124): the scales keep both
+  // within 2^(E - 2 - HEAD) and 2^(E - 1 - HEAD)
+  constexpr int HEAD = Digit<F8>::HEAD;
+  pow2_factors(LB - ((int)emax - 124 + HEAD), s1t, s2t);
+  pow2_factors(LB - ((int)emax - 123 + HEAD), s1tt, s2tt);
   DT* tts = (DT*)(ws + F.tts);
   DT* ts = (DT*)(ws + F.ts);
   const long long plane = (long long)o * v * ldd;
@@ -515,15 +524,61 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 
 // ------------------------------------------------------------------ host
 
+namespace {
+
+// Tile shapes a launch of `slices` digit planes can take: the configured one first, then
+// every other (n_tile, K per stage) the kernel is built for whose level accumulators fit
+// the 512 TMEM columns (BF16: 48..96 columns x K 32 or 16; FP8: 32..64 columns); a
+// non-zero option pins that dimension.
+std::vector<SplitLaunch> shape_candidates(int slices, bool fp8, int n_tile, int stage_k) {
+  std::vector<SplitLaunch> c;
+  c.push_back(split_launch_config(slices, stage_k ? stage_k : 32, n_tile, fp8));
+  auto add = [&](const SplitLaunch& x) {
+    for (const auto& y : c)
+      if (y.n_tile_max == x.n_tile_max && y.bk == x.bk) return;
+    c.push_back(x);
+  };
+  if (fp8) {
+    for (int nt : {64, 48, 32})
+      if ((n_tile == 0 || n_tile == nt) && slices * nt <= 512) {
+        const SplitLaunch x = split_launch_config(slices, 64, nt, true);
+        if (x.n_tile_max == nt) add(x);
+      }
+  } else {
+    for (int bk : {32, 16})
+      for (int nt : {64, 48, 80, 96})
+        if ((stage_k == 0 || stage_k == bk) && (n_tile == 0 || n_tile == nt)) {
+          const SplitLaunch x = split_launch_config(slices, bk, nt, false);
+          if (x.n_tile_max == nt && slices * nt <= 512) add(x);
+        }
+  }
+  return c;
+}
+
+}  // namespace
+
+void split_set_shapes(SplitPlan& sp, int iv, int it, int ig) {
+  auto pick = [](const std::vector<SplitLaunch>& c, int i) {
+    return std::max(0, std::min(i, (int)c.size() - 1));
+  };
+  sp.shape_v = pick(sp.cand_v, iv);
+  sp.shape_t = pick(sp.cand_t, it);
+  sp.shape_g = pick(sp.cand_g, ig);
+  sp.cfg_v = sp.cand_v[sp.shape_v];
+  sp.cfg_t = sp.cand_t[sp.shape_t];
+  sp.cfg_g = sp.cand_g[sp.shape_g];
+}
+
 int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.precision = precision;
   sp.slices_v = opt.slices_v;
   sp.slices_t = opt.slices_t;
   sp.slices_g = opt.slices_g;
   sp.fp8 = precision == RIMP2_FP8_SPLIT;
-  sp.cfg_v = split_launch_config(sp.slices_v, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
-  sp.cfg_t = split_launch_config(sp.slices_t, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
-  sp.cfg_g = split_launch_config(sp.slices_g, opt.stage_k ? opt.stage_k : 32, opt.n_tile, sp.fp8);
+  sp.cand_v = shape_candidates(sp.slices_v, sp.fp8, opt.n_tile, opt.stage_k);
+  sp.cand_t = shape_candidates(sp.slices_t, sp.fp8, opt.n_tile, opt.stage_k);
+  sp.cand_g = shape_candidates(sp.slices_g, sp.fp8, opt.n_tile, opt.stage_k);
+  split_set_shapes(sp, 0, 0, 0);
   sp.grid = split_gemm_grid();
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   sp.ready = true;
@@ -605,6 +660,21 @@ void choose_split_k(SplitProb& P, int grid, int mul) {
   P.ksplit = std::max(1, (P.k1_count + chunk - 1) / chunk);
 }
 
+// Tensor-core FLOPs one problem issues: 2 x 128 x n_tile x K per computed tile (the
+// skip rules of the kernel's tile decoder: V keeps tiles with some row >= some column,
+// symmetric accumulations tiles with some row <= some column) x the digit products.
+double prob_mma_flops(const SplitProb& P, int slices, int bk) {
+  long long tiles = 0;
+  for (int tm = 0; tm < P.tiles_m; ++tm)
+    for (int tn = 0; tn < P.tiles_n; ++tn) {
+      bool skip = P.kind == PK_V && tm * SG_BM + SG_BM - 1 < tn * P.n_tile;
+      if (P.sym) skip = tm * SG_BM > tn * P.n_tile + P.n_tile - 1;
+      tiles += !skip;
+    }
+  const double K = (double)P.k1_count * P.k0_blocks * bk;
+  return (double)tiles * 2.0 * SG_BM * P.n_tile * K * (slices * (slices + 1) / 2);
+}
+
 void finish(std::vector<SplitProb>& v, long long& total) {
   std::stable_sort(v.begin(), v.end(), [](const SplitProb& a, const SplitProb& b) {
     return (double)a.k0_blocks * a.k1_chunk > (double)b.k0_blocks * b.k1_chunk;
@@ -634,6 +704,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   const int sv = sp.slices_v, st = sp.slices_t, sgl = sp.slices_g;
   const int split_mul = sp.variant == 2 ? 4 : 2;
   const bool pij_direct = sp.variant == 1;
+  // exponents of the Tt and T digit planes: the stored max |T| exponent plus these (the
+  // amplitude kernel's scales)
+  const int head = sp.fp8 ? SG_HEAD_FP8 : SG_HEAD_BF16;
+  const int kTtAdd = -123 + head, kTAdd = -124 + head;
   w.want_gamma = false;
   for (int idx : members) {
     const rimp2_frag& f = frags[idx];
@@ -725,7 +799,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       }
       // the leading s_g planes of Tt (one scale per fragment) and B with one scale per aux
       // index Q
-      P.ea_rows = 0; P.ea_off = s.scal + 4; P.ea_add = -123;
+      P.ea_rows = 0; P.ea_off = s.scal + 4; P.ea_add = kTtAdd;
       P.eb_rows = 1; P.eb_off = s.ecol; P.eb_add = 0;
       P.c_off = f.gamma_off; P.ldc = X; P.alpha = 1.0;
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
@@ -748,7 +822,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.k0_blocks = (RL + BKt - 1) / BKt; P.k1_count = o;
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
-      P.ea_add = -123; P.eb_add = -124;
+      P.ea_add = kTtAdd; P.eb_add = kTAdd;
       P.c_off = f.pab_off; P.ldc = v; P.alpha = 1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
@@ -768,7 +842,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.k0_blocks = (vpad + BKt - 1) / BKt; P.k1_count = o * v;
       P.a_mode = P.b_mode = TM_5D; P.div5 = v;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
-      P.ea_add = -123; P.eb_add = -124;
+      P.ea_add = kTtAdd; P.eb_add = kTAdd;
       P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
@@ -790,7 +864,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       P.k0_blocks = (vpad + BKt - 1) / BKt; P.k1_count = o * v;
       P.a_mode = P.b_mode = TM_4D; P.div5 = 1;
       P.ea_rows = P.eb_rows = 0; P.ea_off = P.eb_off = s.scal + 4;
-      P.ea_add = -123; P.eb_add = -124;
+      P.ea_add = kTtAdd; P.eb_add = kTAdd;
       P.c_off = f.pij_off; P.ldc = o; P.alpha = -1.0; P.sym = 1;
       choose_split_k(P, sp.grid, split_mul);
       P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
@@ -810,6 +884,10 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   finish(w.probs_v, w.tiles_v);
   finish(w.probs_c, w.tiles_c);
   finish(w.probs_g, w.tiles_g);
+  w.mma_v = w.mma_c = w.mma_g = 0.0;
+  for (const auto& P : w.probs_v) w.mma_v += prob_mma_flops(P, sv, BKv);
+  for (const auto& P : w.probs_c) w.mma_c += prob_mma_flops(P, st, BKt);
+  for (const auto& P : w.probs_g) w.mma_g += prob_mma_flops(P, sgl, BKg);
   return RIMP2_OK;
 }
 
@@ -892,13 +970,14 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
                           ctr + 1, sp.cfg_t, sp.grid, s);
     ++nl;
   }
+  if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_g > 0) {
     e = launch_split_gemm((const SplitProb*)(dblk + w.off_pg), (const long long*)(dblk + w.off_bg),
                           (int)w.probs_g.size(), w.tiles_g, bs,
                           ctr + 2, sp.cfg_g, sp.grid, s);
     ++nl;
   }
-  if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[5], s, cudaEventRecordExternal);
   *launches = nl;
   *tiles = w.tiles_v + w.tiles_c + w.tiles_g;
   return e == cudaSuccess ? RIMP2_OK : RIMP2_ERR_CUDA;

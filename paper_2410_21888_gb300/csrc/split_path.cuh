@@ -44,7 +44,15 @@ struct SplitPlan {
   bool ready = false;
   bool fp8 = false;  // RIMP2_FP8_SPLIT: e4m3 digits
   int variant = 0;   // contraction-stage variant (autotuner), see split_variant_desc
+  // tile shapes (n_tile, K per stage) the autotuner trials per launch, the configured
+  // default first, and the index of each launch's shape in use
+  std::vector<SplitLaunch> cand_v, cand_t, cand_g;
+  int shape_v = 0, shape_t = 0, shape_g = 0;
 };
+
+// Selects the tile shapes of the V, P_ab / P_ij and Gamma launches (indices into the
+// candidate lists, clamped to their ends).
+void split_set_shapes(SplitPlan& sp, int iv, int it, int ig);
 
 // Variants of the Gamma/P contraction stage the autotuner times:
 //   0: P_ij rows read through the local (k,b)-major view, split-K target 2 x grid
@@ -59,6 +67,7 @@ struct SplitWave {
   std::vector<SplitProb> probs_v, probs_c, probs_g;   // V; P_ab / P_ij; Gamma
   long long tiles_v = 0, tiles_c = 0, tiles_g = 0, rows = 0, b2_tiles = 0, qblks = 0;
   bool want_gamma = false;
+  double mma_v = 0, mma_c = 0, mma_g = 0;   // tensor-core FLOPs issued per launch
   size_t off_sfd = 0, off_pv = 0, off_pc = 0, off_pg = 0;  // byte offsets in the device block
   size_t off_bv = 0, off_bc = 0, off_bg = 0;  // the problems' tile_begin values (int64 each)
 };

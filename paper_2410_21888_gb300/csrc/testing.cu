@@ -8,6 +8,14 @@
 
 using namespace rimp2;
 
+extern "C" int rimp2_testing_set_wait_limit(int64_t ns) {
+  if (split_gemm_set_consumer_wait((long long)ns) != cudaSuccess) {
+    cudaGetLastError();
+    return RIMP2_ERR_CUDA;
+  }
+  return RIMP2_OK;
+}
+
 extern "C" int rimp2_testing_slice_gemm(int32_t M, int32_t N, int32_t K, int32_t kpad,
                                         int32_t slices, const void* A, const void* B, double* C,
                                         void* stream) {
@@ -24,7 +32,7 @@ extern "C" int rimp2_testing_slice_gemm_k(int32_t M, int32_t N, int32_t K, int32
   cudaStream_t s = (cudaStream_t)stream;
   if (!fp8 && stage_k != 16 && stage_k != 32) return RIMP2_ERR_BAD_ARG;
   const SplitLaunch cfg = split_launch_config(slices, stage_k, 0, fp8 != 0);
-  const int E8 = fp8 ? 5 : 8;        // EA = EB = bits per digit: product scale 2^0
+  const int E8 = fp8 ? SG_LB_FP8 : SG_LB_BF16;   // EA = EB = bits per digit: product scale 2^0
   const int esz = fp8 ? 1 : 2;
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
   SplitProb P;

@@ -55,7 +55,7 @@ class Batch(ctypes.Structure):
                 ("frags", ctypes.POINTER(Frag)), ("B", ctypes.c_void_p), ("eps", ctypes.c_void_p),
                 ("gamma", ctypes.c_void_p), ("pij", ctypes.c_void_p), ("pab", ctypes.c_void_p),
                 ("epair", ctypes.c_void_p), ("energy", ctypes.c_void_p),
-                ("energy_os", ctypes.c_void_p)]
+                ("energy_os", ctypes.c_void_p), ("energy_scs", ctypes.c_void_p)]
 
 
 class Options(ctypes.Structure):
@@ -64,7 +64,8 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("profile_stages", ctypes.c_int32),
                 ("max_workspace_bytes", ctypes.c_size_t), ("stage_k", ctypes.c_int32),
                 ("n_tile", ctypes.c_int32), ("autotune_cache", ctypes.c_char_p),
-                ("slices_g", ctypes.c_int32)]
+                ("slices_g", ctypes.c_int32), ("scs_os", ctypes.c_double),
+                ("scs_ss", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +74,11 @@ class Stats(ctypes.Structure):
                 ("launches_per_call", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("graph_captures", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("tune_variant", ctypes.c_int32), ("tune_done", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double * 4), ("stage_ms", ctypes.c_double * 4)]
+                ("tune_ms", ctypes.c_double * 4), ("stage_ms", ctypes.c_double * 4),
+                ("slices", ctypes.c_int32 * 3), ("pad", ctypes.c_int32),
+                ("launch_ms", ctypes.c_double * 2), ("tc_flops", ctypes.c_double * 4),
+                ("n_tile", ctypes.c_int32 * 3), ("stage_k", ctypes.c_int32 * 3),
+                ("tune_trials", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 _lib = None
@@ -151,7 +156,9 @@ class Plan:
     80, 96) and ``stage_k`` (16, 32) shape the tensor-core tiles; ``profile_stages``
     records per-stage device times (``stats().stage_ms``); ``autotune`` times the
     contraction-stage variants in situ, optionally cached in ``autotune_cache``;
-    ``max_workspace_bytes`` splits a large batch into waves.
+    ``max_workspace_bytes`` splits a large batch into waves; ``scs_os`` / ``scs_ss`` are
+    the spin-component weights of the ``energy_scs`` output (None: the library default,
+    Grimme's SCS-MP2).
     """
 
     def __init__(self, dims: Sequence[tuple], precision: str = "fp64", slices_v: int = 0,
@@ -159,7 +166,7 @@ class Plan:
                  max_workspace_bytes: int = 0, profile_stages: bool = False,
                  want_gamma: bool = True, want_p: bool = True, autotune: bool = False,
                  autotune_cache: str | None = None, stage_k: int = 0, n_tile: int = 0,
-                 slices_g: int = 0):
+                 slices_g: int = 0, scs_os: float | None = None, scs_ss: float | None = None):
         _require_cuda()
         lib = load()
         self.dims = [tuple(int(x) for x in d) for d in dims]
@@ -177,6 +184,10 @@ class Plan:
         opt.autotune = int(autotune)
         opt.stage_k = int(stage_k)
         opt.n_tile = int(n_tile)
+        if scs_os is not None:
+            opt.scs_os = float(scs_os)
+        if scs_ss is not None:
+            opt.scs_ss = float(scs_ss)
         self._cache = autotune_cache.encode() if autotune_cache else None
         opt.autotune_cache = self._cache
         h = ctypes.c_void_p()
@@ -247,6 +258,7 @@ class Engine:
         self.epair = torch.zeros(max(npij, 1), **f64) if want_epair else None
         self.energy = torch.zeros(max(len(self.dims), 1), **f64)
         self.energy_os = torch.zeros(max(len(self.dims), 1), **f64)   # opposite-spin part
+        self.energy_scs = torch.zeros(max(len(self.dims), 1), **f64)  # spin-component scaled
         ws = self.plan.workspace_size()
         self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
         self._frags = (Frag * max(1, len(self.dims)))()
@@ -276,6 +288,7 @@ class Engine:
         self._batch.epair = self.epair.data_ptr() if want_epair else None
         self._batch.energy = self.energy.data_ptr()
         self._batch.energy_os = self.energy_os.data_ptr()
+        self._batch.energy_scs = self.energy_scs.data_ptr()
 
     def set_inputs(self, frags, non_blocking=False):
         """frags: sequence of objects with .B [o][v][X], .eo, .ev (numpy or torch)."""
@@ -298,7 +311,8 @@ class Engine:
         """Per-fragment views of the output pools (device tensors)."""
         o, v, X = self.dims[k]
         b, e, pij, pab = self.offsets[k]
-        out = {"energy": self.energy[k], "energy_os": self.energy_os[k]}
+        out = {"energy": self.energy[k], "energy_os": self.energy_os[k],
+               "energy_scs": self.energy_scs[k]}
         if self.gamma is not None:
             out["gamma"] = self.gamma[b:b + o * v * X].view(o, v, X)
         if self.pij is not None:
@@ -333,10 +347,14 @@ def energy_grad(B, eo, ev, precision: str = "fp64", want_gamma=True, want_p=True
     return out
 
 
-def scs_energy(energy, energy_os, c_os: float = 6.0 / 5.0, c_ss: float = 1.0 / 3.0):
-    """Spin-component-scaled MP2 energy from the library's two outputs:
-    c_os E_OS + c_ss E_SS with E_SS = E - E_OS (default weights: Grimme's SCS-MP2)."""
-    return c_os * energy_os + c_ss * (energy - energy_os)
+def scs_energy(B, eo, ev, precision: str = "fp64", c_os: float | None = None,
+               c_ss: float | None = None, **plan_opts):
+    """Spin-component-scaled MP2 energy c_os E_OS + c_ss E_SS of one fragment, formed by
+    the library (batch.energy_scs; default weights: Grimme's SCS-MP2).  Returns the
+    device scalar."""
+    out = energy_grad(B, eo, ev, precision=precision, want_gamma=False, want_p=False,
+                      scs_os=c_os, scs_ss=c_ss, **plan_opts)
+    return out["energy_scs"]
 
 
 # ---------------------------------------------------------------- MBE3 (include/rimp2_mbe.h)

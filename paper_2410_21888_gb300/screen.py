@@ -269,6 +269,54 @@ def screen_and_audit(system, screen: TrimerScreen, ts: TrimerSet, threshold=1e-7
     return res, skip
 
 
+def _prefix_within(order, dE, budget_Eh):
+    """Length of the longest prefix of `order` whose skipped absolute corrections sum to at
+    most budget_Eh (a bound on the change of the MBE3 total)."""
+    return int(np.searchsorted(np.cumsum(np.abs(dE[order])), budget_Eh, side="right"))
+
+
+def compare_with_distance_cutoff(system, ts: TrimerSet, pred_log10, budget_Eh=1e-6):
+    """The method without the screen is a distance cutoff (the paper's reference-monomer
+    cutoff study in Sec. "Molecular Fragmentation"): a trimer is computed when its
+    centroid distances are within R_cut.  For each ordering of the candidates, the
+    trimers are skipped in that order while the sum of their exact |corrections| (a bound
+    on the change of the MBE3 total) stays within budget_Eh, i.e. each rule gets its best
+    threshold in hindsight:
+      distance_max:  farthest first by the largest pairwise centroid distance (R_cut on
+                     the max rule);
+      distance_two:  farthest first by the second-largest distance (R_cut on the two-pair
+                     rule that formed the candidates);
+      learned:       smallest predicted |dE_IJK| first;
+      exact:         smallest exact |dE_IJK| first (the most any ordering can skip).
+    Returns, per ordering, the trimers skipped, their share of the trimer FLOPs and the
+    distance of the last skipped trimer (the equivalent R_cut)."""
+    dE = ts.dE.cpu().numpy()
+    c = np.asarray(system.centroids)
+    t = np.asarray(ts.trimers)
+    d = np.stack([np.linalg.norm(c[t[:, 0]] - c[t[:, 1]], axis=1),
+                  np.linalg.norm(c[t[:, 0]] - c[t[:, 2]], axis=1),
+                  np.linalg.norm(c[t[:, 1]] - c[t[:, 2]], axis=1)], axis=1)
+    d.sort(axis=1)
+    fl = np.array([_flops(system, x) for x in t])
+    orders = {"distance_max": np.argsort(-d[:, 2], kind="stable"),
+              "distance_two": np.argsort(-d[:, 1], kind="stable"),
+              "learned": np.argsort(np.asarray(pred_log10, dtype=np.float64), kind="stable"),
+              "exact": np.argsort(np.abs(dE), kind="stable")}
+    out = {"budget_Eh": budget_Eh, "candidates": int(len(dE))}
+    for name, order in orders.items():
+        k = _prefix_within(order, dE, budget_Eh)
+        sk = order[:k]
+        r = {"skipped": k, "trimer_flop_fraction_skipped": float(fl[sk].sum() / max(fl.sum(), 1.0)),
+             "skipped_sum_Eh": float(dE[sk].sum())}
+        if name.startswith("distance") and k:
+            col = 2 if name == "distance_max" else 1
+            r["equivalent_r_cut_bohr"] = float(d[order[k - 1], col])
+        out[name] = r
+    best_d = max(out["distance_max"]["skipped"], out["distance_two"]["skipped"])
+    out["learned_gain_over_best_distance"] = out["learned"]["skipped"] - best_d
+    return out
+
+
 def _flops(system, t):
     o, v, X = system.fragment_dims(t)
     return float(o * (o + 1) * v * v * X)

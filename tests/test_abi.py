@@ -100,3 +100,16 @@ def test_zvec_host_validation_without_gpu(lib):
     assert lib.rimp2_zvec_solve(ctypes.byref(a), ctypes.c_void_p(4096), 16, None) == -5
     a.tol = -1.0
     assert lib.rimp2_zvec_solve(ctypes.byref(a), ctypes.c_void_p(4096), 1 << 30, None) == -1
+
+
+def test_default_options_without_gpu(lib):
+    """rimp2_default_options fills the struct the binding mirrors field by field: the
+    SCS-MP2 weights (Grimme's 6/5 and 1/3) sit after the last integer option."""
+    from paper_2410_21888_gb300 import rimp2
+    lib.rimp2_default_options.argtypes = [ctypes.POINTER(rimp2.Options)]
+    lib.rimp2_default_options.restype = None
+    o = rimp2.Options()
+    o.slices_g = 77
+    lib.rimp2_default_options(ctypes.byref(o))
+    assert o.use_graph == 1 and o.check_inputs == 1 and o.slices_g == 0
+    assert o.scs_os == 6.0 / 5.0 and o.scs_ss == 1.0 / 3.0

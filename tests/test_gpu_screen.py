@@ -2,7 +2,9 @@
 (split path with 8 slices, FP64-level), the network trained by the library's kernels,
 then candidate trimers of an unseen system screened at 1e-7 Eh.  The test shows the gain
 (trimers and trimer FLOPs skipped) and that the MBE3 total moves by at most 1e-6 Eh; a
-5% sample of the skipped trimers is recomputed by the FP64 path as the audit.
+5% sample of the skipped trimers is recomputed by the FP64 path as the audit; and, at
+the same 1e-6 Eh budget, the learned ordering skips more trimers than the best distance
+cutoff, the rule the screen replaces.
 """
 import numpy as np
 import pytest
@@ -66,3 +68,14 @@ def test_screen_gain_and_error_bound():
     assert abs(res["skipped_sum_Eh"]) <= 1e-6, res
     assert res["audit_count"] >= 1 and res["audit_max_abs_Eh"] < 1e-6, res
     assert res["audit_vs_method_max_diff_Eh"] < 1e-9, res
+    # against the method without the screen: the best distance cutoff (max-pair or
+    # two-pair distance, threshold chosen in hindsight) at the same 1e-6 Eh budget skips
+    # fewer trimers than the learned ordering; no ordering beats the exact one
+    cmp = screen.compare_with_distance_cutoff(_sys(20), test, sc.predict(test.feats).cpu().numpy(),
+                                              1e-6)
+    best_d = max(cmp["distance_max"]["skipped"], cmp["distance_two"]["skipped"])
+    assert cmp["learned"]["skipped"] > best_d, cmp
+    assert cmp["learned_gain_over_best_distance"] > 0, cmp
+    assert cmp["exact"]["skipped"] >= cmp["learned"]["skipped"], cmp
+    for k in ("distance_max", "distance_two", "learned", "exact"):
+        assert abs(cmp[k]["skipped_sum_Eh"]) <= 1e-6, cmp

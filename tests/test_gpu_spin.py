@@ -23,8 +23,12 @@ def test_spin_components_match_oracle(dims, seed, precision):
     tol = 1e-11 * abs(e_os) if precision == "fp64" else 1e-8
     assert abs(Eos - e_os) <= tol, (Eos, e_os)
     assert abs((E - Eos) - e_ss) <= tol + 1e-11 * abs(e_ss), (E - Eos, e_ss)
-    scs = rimp2.scs_energy(E, Eos)
+    # SCS-MP2 combination formed by the library: default (Grimme) and SOS-MP2 weights
+    scs = float(out["energy_scs"].item())
     assert scs == pytest.approx(1.2 * e_os + e_ss / 3.0, abs=2 * tol + 1e-12)
+    sos = float(rimp2.scs_energy(f.B, f.eo, f.ev, precision=precision, c_os=1.3,
+                                 c_ss=0.0).item())
+    assert sos == pytest.approx(1.3 * e_os, abs=2 * tol + 1e-12)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "bf16"])

@@ -1,11 +1,12 @@
 """GPU tests of the split-precision (BF16 integer-slice, tcgen05) path.
 
-1. The tensor-core slice GEMM alone against exact integer arithmetic: digits in
-   [-128, 128], level sums 2^(-8(p+q)) sum_k A_p B_q for p + q < s.  Levels 0 and 1 of
-   each 512-long K chunk are exact integers in FP32 (higher levels too unless a partial
-   sum passes 2^24); levels 0..2 are folded into a double-float accumulator exactly,
-   levels >= 3 in FP32, so the result matches the exact value to ~2^-46 of the absolute
-   digit products.
+1. The tensor-core slice GEMM alone against exact integer arithmetic: BF16 digits in
+   [-64, 64] for the leading slice and [-256, 256] for the others, level sums
+   2^(-9(p+q)) sum_k A_p B_q for p + q < s.  Levels 0 and 1 of each 512-long K chunk are
+   exact integers in FP32 (|S_1| <= 512 * 2 * 2^6 * 2^8 = 2^24; higher levels too unless
+   a partial sum passes 2^24); levels 0..2 are folded into a double-float accumulator
+   exactly, levels >= 3 in FP32, so the result matches the exact value to ~2^-46 of the
+   absolute digit products.
 2. Fragments through rimp2_energy_grad(precision=BF16_SPLIT) against the FP64 oracle.
    Tolerances: energy within 1e-8 Eh per fragment; Gamma, P_ij, P_ab, pair energies
    within 1e-9 relative Frobenius (the accuracy target of the split path).
@@ -39,10 +40,10 @@ def _hook():
     return f
 
 
-def _exact_levels(A, B, s, chunk=512, bits=8):
-    """sum_{p+q<s} 2^(-8(p+q)) A_p B_q^T with exact int64 level sums, and the magnitude
-    the kernel's rounding is relative to: sum over 512-long K chunks and levels of
-    2^(-8 l) sum_k |A_p||B_q| (the usual dot-product error model)."""
+def _exact_levels(A, B, s, chunk=512, bits=9):
+    """sum_{p+q<s} 2^(-bits (p+q)) A_p B_q^T with exact int64 level sums, and the
+    magnitude the kernel's rounding is relative to: sum over K chunks and levels of
+    2^(-bits l) sum_k |A_p||B_q| (the usual dot-product error model)."""
     M, N, K = A.shape[1], B.shape[1], A.shape[2]
     out = np.zeros((M, N))
     mag = np.zeros((M, N))
@@ -74,11 +75,15 @@ def _exact_levels(A, B, s, chunk=512, bits=8):
 def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     rng = np.random.default_rng(seed)
     kpad = (K + 7) // 8 * 8
-    A = rng.integers(-128, 129, size=(s, M, K))
-    B = rng.integers(-128, 129, size=(s, N, K))
-    if seed == 0:                       # worst case for exactness: all products 2^14
-        A[:] = 128
-        B[:] = -128
+    A = rng.integers(-256, 257, size=(s, M, K))
+    B = rng.integers(-256, 257, size=(s, N, K))
+    A[0] = rng.integers(-64, 65, size=(M, K))   # the leading digit is two bits narrower
+    B[0] = rng.integers(-64, 65, size=(N, K))
+    if seed == 0:     # worst case for exactness: level 1 reaches 2^24 in each chunk
+        A[:] = 256
+        B[:] = -256
+        A[0] = 64
+        B[0] = -64
     Ap = np.zeros((s, M, kpad)); Ap[:, :, :K] = A
     Bp = np.zeros((s, N, kpad)); Bp[:, :, :K] = B
     Ad = torch.tensor(Ap, dtype=torch.bfloat16, device="cuda")
@@ -92,7 +97,7 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
     got = C.cpu().numpy()
     assert np.all(np.isfinite(got))
     # an FP32 accumulator alone would err by ~2^-24 of mag and one wrong integer in
-    # levels 0..2 by >= 2^-16 (absolute); demand 2^-44 of the absolute products
+    # levels 0..2 by >= 2^-18 (absolute); demand 2^-44 of the absolute products
     bound = 2.0 ** -44 * (mag + 1.0)
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
 
@@ -121,7 +126,7 @@ def test_fp8_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
     rc = _hook()(M, N, K, kpad, s, 64, 1, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
                  torch.cuda.current_stream().cuda_stream)
     assert rc == 0
-    ref, mag = _exact_levels(A, B, s, bits=5)
+    ref, mag = _exact_levels(A, B, s, chunk=512, bits=5)
     got = C.cpu().numpy()
     bound = 2.0 ** -44 * (mag + 1.0)
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
@@ -162,8 +167,8 @@ def test_split_fragment_parity(dims, seed, mode):
 
 @pytest.mark.parametrize("dims,seed", [((10, 40, 150), 0), ((13, 333, 150), 8)])
 def test_split_fragment_parity_48_column_tiles(dims, seed):
-    """n_tile 48: V (5 slices) then keeps two accumulator sets in TMEM (2 x 240 columns)
-    and alternates between them chunk by chunk; Gamma/P (6 slices) uses one set."""
+    """n_tile 48: V and Gamma (5 slices) keep two accumulator sets in TMEM (2 x 240
+    columns) and alternate between them chunk by chunk; P (6 slices) uses one set."""
     f = synth.fragment_inputs(*dims, seed=seed)
     check_split(rimp2.energy_grad(f.B, f.eo, f.ev, precision="bf16", n_tile=48),
                 oracle.fragment(f.B, f.eo, f.ev))
@@ -268,7 +273,7 @@ def test_diagonal_dominated_energy_has_no_one_signed_error(dims, precision, sv, 
     """With naux >> nocc*nvir most of E comes from the diagonal V_ii(a,a) = sum_Q B^2,
     whose two operands have identical digits.  Were it taken from the truncated product
     triangle, the squared middle digit of the first dropped even level (BF16 4 slices:
-    level 4, 2^-32; FP8 8 slices: level 8, 2^-40) would shift E by ~2e-9 and ~1e-11
+    level 4, 2^-36; FP8 8 slices: level 8, 2^-40) would shift E by ~1e-10 and ~1e-11
     relative; from the FP64 row sum it stays at the random truncation level."""
     f = synth.fragment_inputs(*dims, seed=5)
     ref = oracle.fragment(f.B, f.eo, f.ev, want=())["energy"]
