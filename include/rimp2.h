@@ -126,12 +126,12 @@ typedef struct rimp2_options {
                                  the workspace stays below this many bytes */
   int32_t stage_k;     /* split modes: K elements per pipeline stage of the tensor-core
                           GEMM, 16 or 32 (0 = default 32) */
-  int32_t n_tile;      /* BF16 split: columns per level accumulator, 48, 64, 80 or 96, at
-                          most the widest that fits TMEM for the slice count (0 = the
-                          widest whose two sets of slices x n_tile accumulator columns fit
-                          the 512 TMEM columns: 96, 80, 64, 48 for 2, 3, 4, 5 slices; 64
-                          for 6 or more).  With two sets the MMAs of one 128-long K chunk
-                          run while the previous chunk is drained */
+  int32_t n_tile;      /* BF16 split: columns per level accumulator of every launch, 48,
+                          64, 80 or 96, at most the widest that fits TMEM for the slice
+                          count.  0 = per launch: V 48 when two sets of slices x 48
+                          accumulator columns fit the 512 TMEM columns (the MMAs of one
+                          512-long K chunk then run while the previous one is drained),
+                          a separate Gamma launch 80, P_ab / P_ij 64 */
   const char* autotune_cache; /* NULL, or a text file "<key> <variant>" per line: a plan
                                  whose key (precision, slices, shapes) is listed starts with
                                  that variant and skips the trials; new results are

@@ -526,13 +526,14 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
 
 namespace {
 
-// Tile shapes a launch of `slices` digit planes can take: the configured one first, then
-// every other (n_tile, K per stage) the kernel is built for whose level accumulators fit
-// the 512 TMEM columns (BF16: 48..96 columns x K 32 or 16; FP8: 32..64 columns); a
-// non-zero option pins that dimension.
-std::vector<SplitLaunch> shape_candidates(int slices, bool fp8, int n_tile, int stage_k) {
+// Tile shapes a launch of `slices` digit planes can take: the default one (n_tile_first,
+// 0: the kernel's default width) first, then every other (n_tile, K per stage) the kernel
+// is built for whose level accumulators fit the 512 TMEM columns (BF16: 48..96 columns x
+// K 32 or 16; FP8: 32..64 columns); non-zero n_tile / stage_k options pin that dimension.
+std::vector<SplitLaunch> shape_candidates(int slices, bool fp8, int n_tile_first, int stage_k,
+                                          int n_tile) {
   std::vector<SplitLaunch> c;
-  c.push_back(split_launch_config(slices, stage_k ? stage_k : 32, n_tile, fp8));
+  c.push_back(split_launch_config(slices, stage_k ? stage_k : 32, n_tile_first, fp8));
   auto add = [&](const SplitLaunch& x) {
     for (const auto& y : c)
       if (y.n_tile_max == x.n_tile_max && y.bk == x.bk) return;
@@ -563,7 +564,8 @@ void split_set_shapes(SplitPlan& sp, int iv, int it, int ig) {
   };
   sp.shape_v = pick(sp.cand_v, iv);
   sp.shape_t = pick(sp.cand_t, it);
-  sp.shape_g = pick(sp.cand_g, ig);
+  // Gamma with P's slice count runs in P's launch: it must take that launch's shape
+  sp.shape_g = sp.slices_g == sp.slices_t ? sp.shape_t : pick(sp.cand_g, ig);
   sp.cfg_v = sp.cand_v[sp.shape_v];
   sp.cfg_t = sp.cand_t[sp.shape_t];
   sp.cfg_g = sp.cand_g[sp.shape_g];
@@ -575,9 +577,20 @@ int split_plan_init(SplitPlan& sp, int precision, const rimp2_options& opt) {
   sp.slices_t = opt.slices_t;
   sp.slices_g = opt.slices_g;
   sp.fp8 = precision == RIMP2_FP8_SPLIT;
-  sp.cand_v = shape_candidates(sp.slices_v, sp.fp8, opt.n_tile, opt.stage_k);
-  sp.cand_t = shape_candidates(sp.slices_t, sp.fp8, opt.n_tile, opt.stage_k);
-  sp.cand_g = shape_candidates(sp.slices_g, sp.fp8, opt.n_tile, opt.stage_k);
+  // Default tile widths per launch (BF16; an n_tile option overrides them): V takes 48
+  // columns when two accumulator sets then fit TMEM, so that its heavy epilogue (T = V/D,
+  // two stores per element) overlaps the next chunk's MMAs; Gamma, with K = nocc x nvir,
+  // takes 80, whose wider B tiles cut its operand traffic; P_ab / P_ij keep 64.  Measured
+  // by the autotuner at nocc=100 nvir=500 naux=1500 (5 / 6 / 5 slices): V 44.8 ms against
+  // 45.8 at 64 columns, Gamma 74 against 80 ms.
+  int nv = opt.n_tile, ng = opt.n_tile;
+  if (!sp.fp8 && opt.n_tile == 0) {
+    nv = 2 * sp.slices_v * 48 <= 512 ? 48 : 0;
+    ng = sp.slices_g * 80 <= 512 && sp.slices_g != sp.slices_t ? 80 : 0;
+  }
+  sp.cand_v = shape_candidates(sp.slices_v, sp.fp8, nv, opt.stage_k, opt.n_tile);
+  sp.cand_t = shape_candidates(sp.slices_t, sp.fp8, opt.n_tile, opt.stage_k, opt.n_tile);
+  sp.cand_g = shape_candidates(sp.slices_g, sp.fp8, ng, opt.stage_k, opt.n_tile);
   split_set_shapes(sp, 0, 0, 0);
   sp.grid = split_gemm_grid();
   if (split_gemm_prepare() != cudaSuccess) { cudaGetLastError(); return RIMP2_ERR_CUDA; }
@@ -699,9 +712,11 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   char* wsb = (char*)ws;
   size_t off = 0;
   long long pairs = 0, rows = 0, b2t = 0, qbl = 0;
-  const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max, NTg = sp.cfg_g.n_tile_max;
-  const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk, BKg = sp.cfg_g.bk;
   const int sv = sp.slices_v, st = sp.slices_t, sgl = sp.slices_g;
+  // Gamma with P's slice count joins P's launch and so takes its tile shape
+  const SplitLaunch& cg = sgl == st ? sp.cfg_t : sp.cfg_g;
+  const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max, NTg = cg.n_tile_max;
+  const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk, BKg = cg.bk;
   const int split_mul = sp.variant == 2 ? 4 : 2;
   const bool pij_direct = sp.variant == 1;
   // exponents of the Tt and T digit planes: the stored max |T| exponent plus these (the
@@ -884,6 +899,15 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   finish(w.probs_v, w.tiles_v);
   finish(w.probs_c, w.tiles_c);
   finish(w.probs_g, w.tiles_g);
+  // every problem's tiles and TMA boxes must match the kernel instance of its launch
+  auto same_shape = [](const std::vector<SplitProb>& v, const SplitLaunch& c) {
+    for (const auto& P : v)
+      if (P.n_tile != c.n_tile_max) return false;
+    return true;
+  };
+  if (!same_shape(w.probs_v, sp.cfg_v) || !same_shape(w.probs_c, sp.cfg_t) ||
+      !same_shape(w.probs_g, sp.cfg_g))
+    return RIMP2_ERR_UNSUPPORTED;
   w.mma_v = w.mma_c = w.mma_g = 0.0;
   for (const auto& P : w.probs_v) w.mma_v += prob_mma_flops(P, sv, BKv);
   for (const auto& P : w.probs_c) w.mma_c += prob_mma_flops(P, st, BKt);
