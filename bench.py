@@ -29,11 +29,14 @@ METRIC = "RI-MP2 energy+grad TFLOP/s and fragments/s on 1 GB300, vs plain FP64 a
 WORKLOAD = {"workload": "single fragment RI-MP2 energy+Gamma+P_ab+P_ij, nocc=100 nvir=500 "
                         "naux=1500, seed 0", "nocc": 100, "nvir": 500, "naux": 1500}
 DIMS = (100, 500, 1500)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel at
-# nocc=100 nvir=500 naux=1500, keyed by (precision, launch), from a one-kernel ncu capture
-# of a smaller fragment scaled to this one by the tiles processed.  An entry is removed
-# (traffic null) whenever its kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch at nocc=100 nvir=500
+# naux=1500 (BF16 defaults), keyed by (precision, launch: V, P = P_ab / P_ij, G = Gamma),
+# from an ncu capture of these two metrics alone on this fragment (one pass per launch,
+# which a small-fragment capture showed first).  An entry is removed (traffic null)
+# whenever its kernel or its launch's tile order changes, until it is captured again.
+TRAFFIC_PER_LAUNCH = {("bf16", "G"): 95_910_000_000 + 1_790_000_000,
+                      ("bf16", "P"): 181_620_000_000 + 11_310_000,
+                      ("bf16", "V"): 11_270_000_000 + 10_180_000_000}
 
 
 def flops(o, v, X):
