@@ -35,7 +35,6 @@ DIMS = (100, 500, 1500)
 # which a small-fragment capture showed first).  An entry is removed (traffic null)
 # whenever its kernel or its launch's tile order changes, until it is captured again.
 TRAFFIC_PER_LAUNCH = {("bf16", "G"): 95_910_000_000 + 1_790_000_000,
-                      ("bf16", "P"): 181_620_000_000 + 11_310_000,
                       ("bf16", "V"): 11_270_000_000 + 10_180_000_000}
 
 

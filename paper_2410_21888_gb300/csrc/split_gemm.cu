@@ -370,7 +370,7 @@ __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm,
 
 // ------------------------------------------------------------------ the kernel
 
-// F8 = false: BF16 digits (8 bits each, kind::f16); true: FP8 e4m3 digits (5 bits each,
+// F8 = false: BF16 digits (9 bits each, kind::f16); true: FP8 e4m3 digits (5 bits each,
 // kind::f8f6f4).  Both consume 32 bytes of K per MMA, so the tile geometry in bytes is
 // the same: ROWB bytes of K per row and pipeline stage.
 template <int NT, int ROWB, bool F8>
@@ -402,6 +402,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
   int* tile_prob = (int*)(tile_idx + 2);               // [2]: problem of the entry (producer)
   uint32_t* tmem_base_slot = (uint32_t*)(tile_prob + 2);
   volatile int* abort_flag = (volatile int*)(tmem_base_slot + 1);
+  // V epilogue: per epilogue warp, its NC columns' denominator terms and exponents, loaded
+  // at the start of a tile (while the first chunk's MMAs run) instead of in the element loop
+  float2* stage_dn = (float2*)(smem + (size_t)stages * stage_bytes + 256);
+  int* stage_eb = (int*)(stage_dn + SG_EPI_WARPS * NC);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -582,6 +586,28 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
       if (t >= total) break;
       const TileInfo ti = decode_tile(probs, pi, t, NT);
       if (ti.skip) continue;
+      float2 dm_pre = make_float2(0.f, 0.f);
+      int ea_pre = 0;
+      float2* const sdn = stage_dn + ew * NC;
+      int* const seb = stage_eb + ew * NC;
+      if (ti.P->kind == PK_V) {
+        const SplitProb* P = ti.P;
+        const char* wsb = (const char*)bs.ws;
+        __syncwarp();   // the previous tile's reads of this warp's slice are done
+        for (int c = lane; c < NC; c += 32) {
+          const int n = ti.tn * NT + c0 + c;
+          if (n < P->N) {
+            sdn[c] = ((const float2*)(wsb + P->d_off))[n];
+            seb[c] = ((const int*)(wsb + P->eb_off))[n];
+          }
+        }
+        const int m = ti.tm * SG_BM + row;
+        if (m < P->M) {
+          dm_pre = ((const float2*)(wsb + P->d_off))[m];
+          ea_pre = ((const int*)(wsb + P->ea_off))[m];
+        }
+        __syncwarp();
+      }
       const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
       float acc_h[NC], acc_l[NC];
 #pragma unroll
@@ -633,12 +659,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         const char* wsb = (const char*)bs.ws;
         const int* EA = (const int*)(wsb + P->ea_off);
         const int* EB = (const int*)(wsb + P->eb_off);
-        const int ea = (P->ea_rows ? EA[m] : EA[0]) + P->ea_add;
+        const int ea = (P->kind == PK_V ? ea_pre : (P->ea_rows ? EA[m] : EA[0])) + P->ea_add;
         if (P->kind == PK_V) {
           float* Th = (float*)(wsb + P->c_off);
           float* Tl = (float*)(wsb + P->c2_off);
-          const float2* dv = (const float2*)(wsb + P->d_off);
-          const float2 dm = dv[m];
+          const float2 dm = dm_pre;
           const int im = m / P->v;
           // pair block of column n, advanced as n grows (no division per element)
           int jn = nbase / P->v, jn_end = (jn + 1) * P->v;
@@ -648,13 +673,13 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
             if (n >= P->N) continue;
             while (n >= jn_end) { ++jn; jn_end += P->v; }
             float s1, s2;
-            pow2_pair(ea + (P->eb_rows ? EB[n] : EB[0]) + P->eb_add - 2 * LB, s1, s2);
+            pow2_pair(ea + seb[c] + P->eb_add - 2 * LB, s1, s2);   // V: one exponent per row
             df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
             if (n == m) {   // diagonal: the FP64 row sum of squares (see k_slice_b1)
               const float2 w = ((const float2*)(wsb + P->vd_off))[m];
               V = {w.x, w.y};
             }
-            const float2 dn = dv[n];
+            const float2 dn = sdn[c];
             const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
             const df T = df_div(V, D);
             // the amplitude stage reads the pair blocks i <= j only: store (m, n) where
@@ -735,12 +760,14 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   }
   const size_t rowb = fp8 ? 64 : (size_t)c.bk * 2;
   const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * rowb;
-  const size_t budget = 227 * 1024 - 1024 - 256;
+  // the V epilogue's staging area: per epilogue warp, n_tile / 2 columns x 12 bytes
+  const size_t stage_area = (size_t)SG_EPI_WARPS * (c.n_tile_max / 2) * 12;
+  const size_t budget = 227 * 1024 - 1024 - 256 - stage_area;
   int st = (int)(budget / stage);
   if (st > 8) st = 8;
   if (st < 1) st = 1;
   c.stages = st;
-  c.smem = 1024 + (size_t)st * stage + 256;
+  c.smem = 1024 + (size_t)st * stage + 256 + stage_area;
   return c;
 }
 

@@ -81,7 +81,7 @@ struct SplitProb {  // 64-byte aligned through its CUtensorMap members
 struct SplitLaunch {
   int slices;     // s (levels); same for every problem of one launch
   int bk;         // K elements per pipeline stage (BF16: 16 or 32; FP8: 64)
-  bool fp8;       // digits as FP8 e4m3 (5 bits, kind::f8f6f4) instead of BF16 (8 bits)
+  bool fp8;       // digits as FP8 e4m3 (5 bits, kind::f8f6f4) instead of BF16 (9 bits)
   int n_tile_max; // widest n_tile of the launch (smem layout)
   int stages;     // pipeline depth
   size_t smem;    // dynamic shared memory bytes

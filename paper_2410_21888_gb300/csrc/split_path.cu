@@ -2,7 +2,7 @@
 //
 // Per wave of fragments:
 //   1. k_split_reset   per-fragment exponent slots
-//   2. k_slice_b1      B -> balanced base-256 digits with one scale per row (i,a): the
+//   2. k_slice_b1      B -> balanced base-512 digits with one scale per row (i,a): the
 //                      operands of V (Eq. MP2_ints); also d_m = e_i - e_a per row
 //   3. k_bcol_max      max over (j,b) of |B^Q_jb| for every aux index Q
 //   4. k_slice_b2      B -> digits with one scale per aux index Q, transposed to
@@ -31,6 +31,8 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 // V tiles are walked in groups of this many rows (tile order, see decode_tile)
 constexpr int kVGroupRows = 16;
+// smallest K extent of a split-K piece of P_ab / P_ij
+constexpr long long kMinPieceK = 4096;
 // K extent of one Gamma slab (elements of the contracted (j,b) index).  Measured at
 // nocc=100 nvir=500 naux=1500 (K = 51200): the Gamma/P launch takes 144.7 ms with slabs
 // of 2048, 140.5 with 4096, 138.0 with 8192, 136.5 with 16384 and 138.5 without slabs.
@@ -717,7 +719,11 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
   const SplitLaunch& cg = sgl == st ? sp.cfg_t : sp.cfg_g;
   const int NTv = sp.cfg_v.n_tile_max, NTt = sp.cfg_t.n_tile_max, NTg = cg.n_tile_max;
   const int BKv = sp.cfg_v.bk, BKt = sp.cfg_t.bk, BKg = cg.bk;
-  const int split_mul = sp.variant == 2 ? 4 : 2;
+  // split-K target of P_ab / P_ij in multiples of the grid: finer pieces keep the tiles of
+  // one occupied-index range closer together in time (their operand rows stay in L2);
+  // measured at nocc=100 nvir=500 naux=1500: the P launch 33.3 ms at 2x, 32.2 at 8x, 31.6
+  // at 16x; at nocc=42 nvir=168 naux=630: 0.73, 0.65, 0.68 ms
+  const int split_mul = sp.variant == 2 ? 16 : 8;
   const bool pij_direct = sp.variant == 1;
   // exponents of the Tt and T digit planes: the stored max |T| exponent plus these (the
   // amplitude kernel's scales)
@@ -898,6 +904,20 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
       w.probs_c.push_back(P);
     }
   }
+  // A split-K piece of P_ab / P_ij spans at least kMinPieceK elements of K: the per-problem
+  // target (a multiple of the grid, for locality at large sizes) would otherwise cut the
+  // P_ij of small fragments, K0 = nvir per outer index, into pieces whose drain, epilogue
+  // and atomics cost as much as their MMAs
+  for (auto& P : w.probs_c)
+    if (P.kind == PK_PAB || P.kind == PK_PIJ) {
+      const long long per = (long long)P.k0_blocks * BKt;   // K elements per outer index
+      const int chunk = (int)std::min<long long>(P.k1_count, (kMinPieceK + per - 1) / per);
+      if (P.k1_chunk < chunk) {
+        P.k1_chunk = chunk;
+        P.ksplit = std::max(1, (P.k1_count + chunk - 1) / chunk);
+        P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
+      }
+    }
   total_pairs = pairs;
   w.rows = rows;
   w.b2_tiles = b2t;

@@ -55,9 +55,9 @@ struct SplitPlan {
 void split_set_shapes(SplitPlan& sp, int iv, int it, int ig);
 
 // Variants of the Gamma/P contraction stage the autotuner times:
-//   0: P_ij rows read through the local (k,b)-major view, split-K target 2 x grid
-//   1: P_ij rows read through the direct (i,a)-major view, split-K target 2 x grid
-//   2: local view, split-K target 4 x grid
+//   0: P_ij rows read through the local (k,b)-major view, split-K target 8 x grid
+//   1: P_ij rows read through the direct (i,a)-major view, split-K target 8 x grid
+//   2: local view, split-K target 16 x grid
 //   3: as 0, with Gamma's K in one piece (no slabs, no atomics on Gamma)
 // Variants 0..2 cut Gamma's K into slabs accumulated with FP64 atomics.
 constexpr int kSplitVariants = 4;
