@@ -494,6 +494,22 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       }
     }
   }
+  // digit columns [32 nt, vpad) that no tile reaches (the padded row segment is longer
+  // than the tiles, e.g. nvir = 1500 with 1536-element segments): zero in every row
+  if (st > 0 && vpad > nt * 32) {
+    using U4 = uint4;
+    const int w16 = (vpad - nt * 32) * (int)sizeof(DT) / 16;   // 16-byte units per row
+    const long long units = (long long)(st + stt) * v * w16;
+    for (long long u = tid; u < units; u += blockDim.x) {
+      long long x = u;
+      const int c = (int)(x % w16); x /= w16;
+      const int a = (int)(x % v);
+      const int p = (int)(x / v);
+      DT* base = p < stt ? ts + p * plane : tts + (p - stt) * plane;
+      DT* row = base + (rowI + a) * ldd + colJ + nt * 32;
+      ((U4*)row)[c] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
   // pair energy: warp, then block, in double-float; one FP64 value per pair
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

@@ -182,6 +182,23 @@ def test_split_gamma_in_two_slabs():
                 oracle.fragment(f.B, f.eo, f.ev))
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_split_padded_row_segments_in_a_dirty_workspace(precision):
+    """nvir = 1120: the digit planes pad each (j, b) row segment to 1152 elements (the
+    widest alignment under 3 % of padding), 32 more than the 32-wide amplitude tiles reach.
+    Those padding columns enter the contractions of P_ab, P_ij and Gamma, so they must be
+    written as zero on every call: the workspace is filled with NaN bytes first."""
+    f = synth.fragment_inputs(2, 1120, 48, seed=13)
+    ref = oracle.fragment(f.B, f.eo, f.ev)
+    eng = rimp2.Engine([f.B.shape], precision=precision)
+    eng.set_inputs([f])
+    eng.workspace.fill_(0xFF)
+    eng.run()
+    torch.cuda.synchronize()
+    eng.check_status()
+    check_split(eng.views(0), ref)
+
+
 def test_split_degenerate_sizes():
     for dims in [(3, 0, 5), (0, 4, 5), (3, 4, 0)]:
         f = synth.fragment_inputs(*dims, seed=0)
