@@ -292,6 +292,44 @@ __device__ __forceinline__ df df_div(df a, df b) {
   return fast_two_sum(s.h, __fadd_rn(s.l, q3));
 }
 
+// Two FP32 lanes in one 64-bit register for the packed f32x2 arithmetic of sm_100+
+// (add/sub/mul/fma.rn.f32x2: each lane rounds exactly like the scalar instruction)
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2x r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// two_sum on two lanes: s = a + b and its exact rounding error
+__device__ __forceinline__ void f2_two_sum(f2x a, f2x b, f2x& s, f2x& e) {
+  s = f2_add(a, b);
+  const f2x bb = f2_sub(s, a);
+  e = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+}
+
 // 2^e as float for e in [-252, 254] via two normal factors
 __device__ __forceinline__ void pow2_pair(int e, float& s1, float& s2) {
   e = max(-252, min(254, e));
@@ -358,6 +396,27 @@ __device__ __forceinline__ TileInfo decode_tile(const SplitProb* __restrict__ pr
   if (ti.P->sym) ti.skip = ti.tm * SG_BM > ti.tn * nt + nt - 1;
   if (ti.skip) ti.nK = 0;
   return ti;
+}
+
+// End of the run of work-free entries that starts at the skipped entry t: for V, when t's
+// column lies right of the diagonal of its whole row group (group raster) or row (row-major
+// order), every later entry of that group or row is skipped too; otherwise t + 1.
+__device__ __forceinline__ long long skipped_run_end(const TileInfo& ti, long long t, int nt) {
+  const SplitProb* P = ti.P;
+  if (P->kind != PK_V) return t + 1;
+  const long long lt = t - P->tile_begin;   // V has no split-K
+  if (P->group_m > 1) {
+    const long long gsz = (long long)P->group_m * P->tiles_n;
+    const long long g = lt / gsz;
+    const int first = (int)g * P->group_m;
+    const int gm = min(P->group_m, P->tiles_m - first);
+    const int tn_max = ((first + gm - 1) * SG_BM + SG_BM - 1) / nt;   // last column with work
+    if (ti.tn > tn_max) return P->tile_begin + g * gsz + (long long)gm * P->tiles_n;
+  } else {
+    const int tn_max = (ti.tm * SG_BM + SG_BM - 1) / nt;
+    if (ti.tn > tn_max) return P->tile_begin + (long long)(ti.tm + 1) * P->tiles_n;
+  }
+  return t + 1;
 }
 
 __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
@@ -458,6 +517,17 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         // the problem search is done here once per entry; the MMA and epilogue warps take
         // its result from shared memory
         const int pi = t < total ? find_problem(probs, begins, nprobs, t) : 0;
+        TileInfo ti{};
+        if (t < total) {
+          ti = decode_tile(probs, pi, t, NT);
+          if (ti.skip) {
+            // a tile without work is not handed on; where it starts a run of them (the
+            // columns of a V row group right of the diagonal), the queue moves past the run
+            const long long run_end = skipped_run_end(ti, t, NT);
+            if (run_end > t + 1) atomicMax(counter, (unsigned)min(run_end, total));
+            continue;
+          }
+        }
         if (!mbar_wait(tile_empty + tslot, tph ^ 1u, abort_flag)) break;
         tile_idx[tslot] = t;
         tile_prob[tslot] = pi;
@@ -465,7 +535,6 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         tslot ^= 1;
         if (tslot == 0) tph ^= 1u;
         if (t >= total) break;
-        const TileInfo ti = decode_tile(probs, pi, t, NT);
         const SplitProb* P = ti.P;
         const int rowA = ti.tm * SG_BM, rowB = ti.tn * NT;
         bool ok = true;
@@ -609,9 +678,10 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         __syncwarp();
       }
       const int chunks = (ti.nK + CHUNK_STAGES - 1) / CHUNK_STAGES;
-      float acc_h[NC], acc_l[NC];
+      // the (hi, lo) accumulators of column pairs, folded with packed f32x2 arithmetic
+      f2x acc_h2[NC / 2], acc_l2[NC / 2];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { acc_h[c] = 0.f; acc_l[c] = 0.f; }
+      for (int c = 0; c < NC / 2; ++c) { acc_h2[c] = 0ull; acc_l2[c] = 0ull; }
       bool ok = true;
       for (int ch = 0; ch < chunks; ++ch) {
         const uint32_t set = cc % nbuf, use = cc / nbuf;
@@ -626,30 +696,40 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
             tmem_ld8(set_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
           tmem_wait_ld();
           const float sc = __int_as_float((127 - LB * l) << 23);   // 2^(-LB l)
+          const f2x sc2 = f2_pack(sc, sc);
           if (l >= EXACT) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc_l[c] = fmaf(v[c], sc, acc_l[c]);
+            for (int c = 0; c < NC / 2; ++c)
+              acc_l2[c] = f2_fma(f2_pack(v[2 * c], v[2 * c + 1]), sc2, acc_l2[c]);
           } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const df s2 = two_sum(acc_h[c], v[c] * sc);
-              acc_h[c] = s2.h;
-              acc_l[c] += s2.l;
+            for (int c = 0; c < NC / 2; ++c) {
+              f2x s2, e2;
+              f2_two_sum(acc_h2[c], f2_mul(f2_pack(v[2 * c], v[2 * c + 1]), sc2), s2, e2);
+              acc_h2[c] = s2;
+              acc_l2[c] = f2_add(acc_l2[c], e2);
             }
           }
         }
         // renormalise so that lo stays within half an ulp of hi across chunks
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const df r = two_sum(acc_h[c], acc_l[c]);
-          acc_h[c] = r.h;
-          acc_l[c] = r.l;
+        for (int c = 0; c < NC / 2; ++c) {
+          f2x s2, e2;
+          f2_two_sum(acc_h2[c], acc_l2[c], s2, e2);
+          acc_h2[c] = s2;
+          acc_l2[c] = e2;
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tmem_empty + set);
       }
       if (!ok) break;
+      float acc_h[NC], acc_l[NC];
+#pragma unroll
+      for (int c = 0; c < NC / 2; ++c) {
+        f2_unpack(acc_h2[c], acc_h[2 * c], acc_h[2 * c + 1]);
+        f2_unpack(acc_l2[c], acc_l[2 * c], acc_l[2 * c + 1]);
+      }
       // ---------------- problem epilogue (registers only; TMEM already released)
       const SplitProb* P = ti.P;
       const int m = ti.tm * SG_BM + row;
