@@ -204,6 +204,24 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Columns c .. c+NC-1 of this warp's 32 TMEM lanes (NC a multiple of 8), issued without
+// waiting; the values are valid after tmem_wait_ld and tmem_hold.
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]) {
+#pragma unroll
+  for (int g = 0; g < NC / 8; ++g) tmem_ld8(taddr + (uint32_t)(g * 8), v + g * 8);
+}
+
+// Ties the registers of an asynchronous TMEM load to the point after tcgen05.wait::ld, so
+// that no computation on them is scheduled before the wait.
+template <int NC>
+__device__ __forceinline__ void tmem_hold(float (&v)[NC]) {
+#pragma unroll
+  for (int g = 0; g < NC / 8; ++g)
+    asm volatile("" : "+f"(v[g * 8 + 0]), "+f"(v[g * 8 + 1]), "+f"(v[g * 8 + 2]), "+f"(v[g * 8 + 3]),
+                 "+f"(v[g * 8 + 4]), "+f"(v[g * 8 + 5]), "+f"(v[g * 8 + 6]), "+f"(v[g * 8 + 7]));
+}
+
 // UMMA shared-memory descriptor of a K-major operand with ROWB-byte rows (64 or 32)
 // and the matching swizzle: 8-row core groups 8 ROWB bytes apart (SBO), descriptor
 // version 1, layout SWIZZLE_64B (4) for 64-byte rows, SWIZZLE_32B (6) for 32-byte rows.
@@ -689,12 +707,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
         const uint32_t set_addr = lane_addr + set * set_cols;
         if (!mbar_wait_warp(tmem_full + set, use & 1u, abort_flag, cwait)) { ok = false; break; }
         tc_fence_after();
-        for (int l = slices - 1; l >= 0; --l) {
-          float v[NC];
-#pragma unroll
-          for (int g = 0; g < NC / 8; ++g)
-            tmem_ld8(set_addr + (uint32_t)(l * NT + c0 + g * 8), v + g * 8);
-          tmem_wait_ld();
+        // levels from the highest down; the set is released as soon as level 0 is in
+        // registers (its fold and the renormalisation run while the next MMAs do).  Up to
+        // 24 columns a thread, two register buffers: the loads of level l-1 are in flight
+        // while level l is folded (wider tiles would spill)
+        auto fold = [&](int l, float (&v)[NC]) {
           const float sc = __int_as_float((127 - LB * l) << 23);   // 2^(-LB l)
           const f2x sc2 = f2_pack(sc, sc);
           if (l >= EXACT) {
@@ -710,6 +727,37 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
               acc_l2[c] = f2_add(acc_l2[c], e2);
             }
           }
+        };
+        auto release = [&]() {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tmem_empty + set);
+        };
+        if constexpr (NC <= 24) {
+          float va[NC], vb[NC];
+          tmem_ld_cols<NC>(set_addr + (uint32_t)((slices - 1) * NT + c0), va);
+          for (int l = slices - 1; l >= 0; l -= 2) {
+            tmem_wait_ld();
+            tmem_hold<NC>(va);
+            if (l >= 1) tmem_ld_cols<NC>(set_addr + (uint32_t)((l - 1) * NT + c0), vb);
+            else release();
+            fold(l, va);
+            if (l == 0) break;
+            tmem_wait_ld();
+            tmem_hold<NC>(vb);
+            if (l >= 2) tmem_ld_cols<NC>(set_addr + (uint32_t)((l - 2) * NT + c0), va);
+            else release();
+            fold(l - 1, vb);
+          }
+        } else {
+          for (int l = slices - 1; l >= 0; --l) {
+            float v[NC];
+            tmem_ld_cols<NC>(set_addr + (uint32_t)(l * NT + c0), v);
+            tmem_wait_ld();
+            tmem_hold<NC>(v);
+            if (l == 0) release();
+            fold(l, v);
+          }
         }
         // renormalise so that lo stays within half an ulp of hi across chunks
 #pragma unroll
@@ -719,9 +767,6 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
           acc_h2[c] = s2;
           acc_l2[c] = e2;
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tmem_empty + set);
       }
       if (!ok) break;
       float acc_h[NC], acc_l[NC];
