@@ -34,9 +34,9 @@ DIMS = (100, 500, 1500)
 # from an ncu capture of these two metrics alone on this fragment (one pass per launch,
 # which a small-fragment capture showed first).  An entry is removed (traffic null)
 # whenever its kernel or its launch's tile order changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {("bf16", "G"): 103_960_000_000 + 1_800_000_000,
-                      ("bf16", "P"): 137_140_000_000 + 27_410_000,
-                      ("bf16", "V"): 11_320_000_000 + 10_180_000_000}
+TRAFFIC_PER_LAUNCH = {("bf16", "G"): 107_330_000_000 + 1_900_000_000,
+                      ("bf16", "P"): 132_760_000_000 + 26_480_000,
+                      ("bf16", "V"): 10_800_000_000 + 10_190_000_000}
 
 
 def flops(o, v, X):
