@@ -9,13 +9,13 @@
 // with 5 in place of 9 in every formula below.
 // C(m,n) = sum_k A(m,k) B(n,k) is then 2^(EA(m) + EB(n) - 2 LB) sum_l 2^(-LB l) S_l with
 // S_l = sum_{p+q=l} sum_k dA_p dB_q, the truncated level sum kept for l < s.  Each S_l
-// accumulates in its own FP32 TMEM accumulator over K chunks of 512, where levels 0 and
-// 1 are exact integers by construction (BF16: |S_0| <= 512 * 2^12 = 2^21 and
-// |S_1| <= 512 * 2 * 2^6 * 2^8 = 2^24, the narrow leading digit is what allows 512;
-// FP8: every level of up to 16 slices stays below 16 * 512 * 2^8 < 2^24); a BF16 level
-// l >= 2 rounds only if its partial sum exceeds 2^24 in magnitude, which bounds that
-// error by 2^-24 of the level.  Each chunk is then folded into a per-element
-// double-float (hi, lo) accumulator in registers.
+// accumulates in its own FP32 TMEM accumulator over K chunks, where the levels folded
+// exactly are exact integers by construction.  BF16, chunks of 512: |S_0| <= 512 * 2^12
+// = 2^21 and |S_1| <= 512 * 2 * 2^6 * 2^8 = 2^24 (the narrow leading digit is what allows
+// 512).  FP8, chunks of 8192: levels 0..4 stay below 5 * 8192 * 2^8 < 2^24.  A higher
+// level rounds only if its partial sum exceeds 2^24 in magnitude, which bounds that error
+// by 2^-24 of the level.  Each chunk is then folded into a per-element double-float
+// (hi, lo) accumulator in registers.
 #pragma once
 
 #include <cuda.h>
@@ -32,7 +32,7 @@ constexpr int SG_BN_MAX = 96;       // max columns per tile
 // digit is narrower than the others (the scale of x is 2^E with |x| <= 2^(E-1-HEAD)), of
 // each digit format
 constexpr int SG_LB_BF16 = 9, SG_CHUNK_K_BF16 = 512, SG_HEAD_BF16 = 2;
-constexpr int SG_LB_FP8 = 5, SG_CHUNK_K_FP8 = 512, SG_HEAD_FP8 = 0;
+constexpr int SG_LB_FP8 = 5, SG_CHUNK_K_FP8 = 8192, SG_HEAD_FP8 = 0;
 // K per pipeline stage: 32 (64-byte rows, 64B swizzle) or 16 (32-byte rows, 32B swizzle);
 // the smaller stage fits twice as many stages in shared memory
 constexpr int SG_MAX_SLICES = 16;   // FP8; BF16 stops at 8

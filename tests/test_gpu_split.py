@@ -104,17 +104,19 @@ def test_slice_gemm_matches_exact_integer_products(M, N, K, s, seed, stage_k):
 
 @pytest.mark.parametrize("M,N,K,s,seed", [
     (128, 64, 64, 8, 0),         # worst case magnitudes, one stage
-    (200, 150, 1100, 8, 1),      # three chunks, ragged
+    (200, 150, 1100, 8, 1),      # one 8192-long chunk, ragged
+    (130, 64, 9000, 10, 4),      # two chunks, the first 8192 long: levels 0..4 near 2^23
     (130, 48, 700, 10, 2),       # ten slices, 48-column tiles
     (140, 40, 600, 16, 3),       # sixteen slices, 32-column tiles, one pipeline stage
 ])
 def test_fp8_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
-    """FP8 e4m3 digits in [-16, 16], 5-bit levels: every level sum of a chunk is exact."""
+    """FP8 e4m3 digits in [-16, 16], 5-bit levels, K chunks of 8192: levels 0..4 of a chunk
+    are exact sums (below 5 * 8192 * 2^8 < 2^24), higher ones within 2^-24 of the level."""
     rng = np.random.default_rng(seed)
     kpad = (K + 15) // 16 * 16
     A = rng.integers(-16, 17, size=(s, M, K))
     B = rng.integers(-16, 17, size=(s, N, K))
-    if seed == 0:
+    if seed in (0, 4):
         A[:] = 16
         B[:] = -16
     Ap = np.zeros((s, M, kpad)); Ap[:, :, :K] = A
@@ -126,7 +128,7 @@ def test_fp8_slice_gemm_matches_exact_integer_products(M, N, K, s, seed):
     rc = _hook()(M, N, K, kpad, s, 64, 1, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
                  torch.cuda.current_stream().cuda_stream)
     assert rc == 0
-    ref, mag = _exact_levels(A, B, s, chunk=512, bits=5)
+    ref, mag = _exact_levels(A, B, s, chunk=8192, bits=5)
     got = C.cpu().numpy()
     bound = 2.0 ** -44 * (mag + 1.0)
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) - bound))
