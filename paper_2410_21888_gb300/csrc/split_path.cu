@@ -198,20 +198,6 @@ __device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* ou
   }
 }
 
-// Digits of an FP64 value x relative to 2^E (|x| <= 2^(E-1)), written to out[p * plane]:
-// x is split once into a double-float (48 significant bits, more than s digits carry),
-// scaled by 2^(LB-E) = s1 * s2 (two normal powers of two), and the digits are taken with
-// digit_step, exact for the double-float.
-template <bool F8>
-__device__ __forceinline__ void digits_b(double x, float s1, float s2, int s,
-                                         typename Digit<F8>::T* out, long long plane) {
-  constexpr int LB = Digit<F8>::LB;
-  const float h = (float)x;
-  const float l = (float)(x - (double)h);
-  float xh = (h * s1) * s2, xl = (l * s1) * s2;
-  for (int p = 0; p < s; ++p) out[p * plane] = Digit<F8>::enc(digit_step<LB>(xh, xl));
-}
-
 // 2^e as two normal powers of two (e clamped to [-252, 254])
 __device__ __forceinline__ void pow2_factors(int e, float& s1, float& s2) {
   e = max(-252, min(254, e));
@@ -264,7 +250,19 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
   DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
   float s1, s2;
   pow2_factors(Digit<F8>::LB - E, s1, s2);
-  for (int q = lane; q < F.X; q += 32) digits_b<F8>(x[q], s1, s2, sv, out + q, plane);
+  // four consecutive elements a lane, one packed store per plane (elements in [X, xpad)
+  // get zero digits; the V operand's tensor map ends at X)
+  for (int q0 = 4 * lane; q0 < F.X; q0 += 128) {
+    dfl xs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double xq = q0 + k < F.X ? x[q0 + k] : 0.0;
+      const float h = (float)xq;
+      const float l = (float)(xq - (double)h);
+      xs[k] = {(h * s1) * s2, (l * s1) * s2};
+    }
+    put4<F8>(xs, sv, out + q0, plane);
+  }
   if (lane == 0) {
     ((int*)(ws + F.erow))[r] = E;
     const int i = r / F.v, a = r - i * F.v;
@@ -307,22 +305,23 @@ k_bcol_max(const SplitFragDev* __restrict__ f, int nf, Bases bs) {
 
 // Gamma's B operand: Bs2[p][Q][c], c = j*vpad + b (zero for b >= nvir), one scale
 // 2^E_Q per aux index, E_Q = ilogb(max_(j,b) |B^Q_jb|) + 2 + HEAD (also stored for the GEMM
-// epilogue).  32 x 32 tiles transposed through shared memory.
+// epilogue).  Tiles of 32 aux indices x 128 columns c transposed through shared memory;
+// each thread then writes four consecutive c of one Q, one packed store per plane.
 template <bool F8>
 __global__ void __launch_bounds__(256)
 k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   using DT = typename Digit<F8>::T;
-  __shared__ double tile[32][33];
+  __shared__ double tile[128][33];
   const long long gt = blockIdx.x;
   const SplitFragDev& F = f[find_sfd(f, nf, gt, 1)];
   const long long lt = gt - F.b2_tile_begin;
   const int RL = F.o * F.vpad;
-  const int ntc = (RL + 31) / 32;
+  const int ntc = (RL + 127) / 128;
   const int tq = (int)(lt / ntc), tc = (int)(lt % ntc);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const double* B = bs.B + F.b_off;
-  for (int r = ty; r < 32; r += 8) {
-    const int c = tc * 32 + r, Q = tq * 32 + tx;
+  for (int r = ty; r < 128; r += 8) {
+    const int c = tc * 128 + r, Q = tq * 32 + tx;
     double val = 0.0;
     if (c < RL && Q < F.X) {
       const int j = c / F.vpad, b = c - j * F.vpad;
@@ -336,17 +335,27 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   int* ec = (int*)(ws + F.ecol);
   const long long plane = (long long)F.X * F.ldd;
   DT* out = (DT*)(ws + F.bs2);
-  for (int r = ty; r < 32; r += 8) {
-    const int Q = tq * 32 + r, c = tc * 32 + tx;
-    if (Q >= F.X) continue;
-    const double mq = __longlong_as_double((long long)cm[Q]);
-    const int E = mq > 0.0 ? ilogb(mq) + 2 + Digit<F8>::HEAD : -1000;
-    if (tc == 0 && tx == 0) ec[Q] = E;
-    if (c < RL) {
-      float s1, s2;
-      pow2_factors(Digit<F8>::LB - E, s1, s2);
-      digits_b<F8>(tile[tx][r], s1, s2, st, out + (long long)Q * F.ldd + c, plane);
+  const int qi = threadIdx.x >> 3, cg = threadIdx.x & 7;
+  const int Q = tq * 32 + qi;
+  if (Q >= F.X) return;
+  const double mq = __longlong_as_double((long long)cm[Q]);
+  const int E = mq > 0.0 ? ilogb(mq) + 2 + Digit<F8>::HEAD : -1000;
+  if (tc == 0 && cg == 0) ec[Q] = E;
+  float s1, s2;
+  pow2_factors(Digit<F8>::LB - E, s1, s2);
+#pragma unroll
+  for (int k4 = 0; k4 < 4; ++k4) {
+    const int cl = k4 * 32 + cg * 4, c = tc * 128 + cl;   // RL is a multiple of 4
+    if (c >= RL) break;
+    dfl xs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double xq = tile[cl + k][qi];
+      const float h = (float)xq;
+      const float l = (float)(xq - (double)h);
+      xs[k] = {(h * s1) * s2, (l * s1) * s2};
     }
+    put4<F8>(xs, st, out + (long long)Q * F.ldd + c, plane);
   }
 }
 
@@ -772,7 +781,7 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
     pairs += (long long)o * o;   // amplitude stage: one CTA per ordered pair
     rows += ov;
     if (g) {
-      b2t += (long long)((X + 31) / 32) * ((RL + 31) / 32);
+      b2t += (long long)((X + 31) / 32) * ((RL + 127) / 128);
       qbl += (long long)((X + 31) / 32) * ((ov + 255) / 256);
       w.want_gamma = true;
     }
