@@ -341,11 +341,50 @@ __device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+__device__ __forceinline__ f2x f2_neg(f2x a) {
+  f2x d;
+  asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(d) : "l"(a));
+  return d;
+}
 // two_sum on two lanes: s = a + b and its exact rounding error
 __device__ __forceinline__ void f2_two_sum(f2x a, f2x b, f2x& s, f2x& e) {
   s = f2_add(a, b);
   const f2x bb = f2_sub(s, a);
   e = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+}
+
+// fast_two_sum on two lanes (|a| >= |b| in each)
+__device__ __forceinline__ void f2_fast_two_sum(f2x a, f2x b, f2x& s, f2x& e) {
+  s = f2_add(a, b);
+  e = f2_sub(b, f2_sub(s, a));
+}
+
+// df_add and df_div on two lanes (two column pairs of double-floats): the same operations
+// in the same order as the scalar versions, so each lane's result is bit-identical; only
+// the correctly rounded quotient and reciprocal run per lane.
+__device__ __forceinline__ void df_add2(f2x ah, f2x al, f2x bh, f2x bl, f2x& h, f2x& l) {
+  f2x sh, sl;
+  f2_two_sum(ah, bh, sh, sl);
+  sl = f2_add(sl, f2_add(al, bl));
+  f2_fast_two_sum(sh, sl, h, l);
+}
+__device__ __forceinline__ void df_div2(f2x ah, f2x al, f2x bh, f2x bl, f2x& h, f2x& l) {
+  float a0, a1, b0, b1;
+  f2_unpack(ah, a0, a1);
+  f2_unpack(bh, b0, b1);
+  const f2x q1 = f2_pack(__fdiv_rn(a0, b0), __fdiv_rn(a1, b1));
+  const f2x rc = f2_pack(__frcp_rn(b0), __frcp_rn(b1));
+  const f2x ph = f2_mul(q1, bh);
+  const f2x pl = f2_fma(q1, bh, f2_neg(ph));
+  const f2x r = f2_fma(f2_neg(q1), bl, f2_add(f2_sub(f2_sub(ah, ph), pl), al));
+  const f2x q2 = f2_mul(r, rc);
+  const f2x ph2 = f2_mul(q2, bh);
+  const f2x pl2 = f2_fma(q2, bh, f2_neg(ph2));
+  const f2x r2 = f2_fma(f2_neg(q2), bl, f2_sub(f2_sub(r, ph2), pl2));
+  const f2x q3 = f2_mul(r2, rc);
+  f2x sh, sl;
+  f2_fast_two_sum(q1, q2, sh, sl);
+  f2_fast_two_sum(sh, f2_add(sl, q3), h, l);
 }
 
 // 2^e as float for e in [-252, 254] via two normal factors
@@ -792,34 +831,83 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
           const int im = m / P->v;
           // pair block of column n, advanced as n grows (no division per element)
           int jn = nbase / P->v, jn_end = (jn + 1) * P->v;
+          const f2x dmh = f2_pack(dm.x, dm.x), dml = f2_pack(dm.y, dm.y);
+          if constexpr (NC > 24) {   // wide tiles: scalar (the packed form would spill)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            const int n = nbase + c;
-            if (n >= P->N) continue;
-            while (n >= jn_end) { ++jn; jn_end += P->v; }
-            float s1, s2;
-            pow2_pair(ea + seb[c] + P->eb_add - 2 * LB, s1, s2);   // V: one exponent per row
-            df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
-            if (n == m) {   // diagonal: the FP64 row sum of squares (see k_slice_b1)
-              const float2 w = ((const float2*)(wsb + P->vd_off))[m];
-              V = {w.x, w.y};
+            for (int c = 0; c < NC; ++c) {
+              const int n = nbase + c;
+              if (n >= P->N) continue;
+              while (n >= jn_end) { ++jn; jn_end += P->v; }
+              float s1, s2;
+              pow2_pair(ea + seb[c] + P->eb_add - 2 * LB, s1, s2);   // V: one exponent per row
+              df V = {(acc_h[c] * s1) * s2, (acc_l[c] * s1) * s2};
+              if (n == m) {   // diagonal: the FP64 row sum of squares (see k_slice_b1)
+                const float2 w = ((const float2*)(wsb + P->vd_off))[m];
+                V = {w.x, w.y};
+              }
+              const float2 dn = sdn[c];
+              const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
+              const df T = df_div(V, D);
+              if (im <= jn) {
+                const long long ix = (long long)m * P->ldc + n + (long long)jn * (P->vpad - P->v);
+                Th[ix] = T.h;
+                Tl[ix] = T.l;
+              }
+              if (jn <= im) {
+                const long long ix = (long long)n * P->ldc + m + (long long)im * (P->vpad - P->v);
+                Th[ix] = T.h;
+                Tl[ix] = T.l;
+              }
+              emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
             }
-            const float2 dn = sdn[c];
-            const df D = df_add({dm.x, dm.y}, {dn.x, dn.y});
-            const df T = df_div(V, D);
-            // the amplitude stage reads the pair blocks i <= j only: store (m, n) where
-            // i(m) <= i(n) and the mirror (n, m) where i(n) <= i(m)
-            if (im <= jn) {
-              const long long ix = (long long)m * P->ldc + n + (long long)jn * (P->vpad - P->v);
-              Th[ix] = T.h;
-              Tl[ix] = T.l;
+          } else {
+            // column pairs in packed f32x2 arithmetic (columns past N are computed from
+            // unused staging entries and not stored)
+  #pragma unroll
+            for (int k = 0; k < NC / 2; ++k) {
+              float s1a, s2a, s1b, s2b;   // V: one exponent per row and per column
+              pow2_pair(ea + seb[2 * k] + P->eb_add - 2 * LB, s1a, s2a);
+              pow2_pair(ea + seb[2 * k + 1] + P->eb_add - 2 * LB, s1b, s2b);
+              const f2x s1 = f2_pack(s1a, s1b), s2 = f2_pack(s2a, s2b);
+              f2x Vh = f2_mul(f2_mul(acc_h2[k], s1), s2), Vl = f2_mul(f2_mul(acc_l2[k], s1), s2);
+              const int n0 = nbase + 2 * k;
+              if (n0 == m || n0 + 1 == m) {   // diagonal: the FP64 row sum of squares (see k_slice_b1)
+                const float2 w = ((const float2*)(wsb + P->vd_off))[m];
+                float h0, h1, l0, l1;
+                f2_unpack(Vh, h0, h1);
+                f2_unpack(Vl, l0, l1);
+                if (n0 == m) { h0 = w.x; l0 = w.y; } else { h1 = w.x; l1 = w.y; }
+                Vh = f2_pack(h0, h1);
+                Vl = f2_pack(l0, l1);
+              }
+              const float2 dna = sdn[2 * k], dnb = sdn[2 * k + 1];
+              f2x Dh, Dl, Th2, Tl2;
+              df_add2(dmh, dml, f2_pack(dna.x, dnb.x), f2_pack(dna.y, dnb.y), Dh, Dl);
+              df_div2(Vh, Vl, Dh, Dl, Th2, Tl2);
+              df Tc[2];
+              f2_unpack(Th2, Tc[0].h, Tc[1].h);
+              f2_unpack(Tl2, Tc[0].l, Tc[1].l);
+  #pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int n = n0 + u;
+                if (n >= P->N) continue;
+                while (n >= jn_end) { ++jn; jn_end += P->v; }
+                const df T = Tc[u];
+                // the amplitude stage reads the pair blocks i <= j only: store (m, n) where
+                // i(m) <= i(n) and the mirror (n, m) where i(n) <= i(m)
+                if (im <= jn) {
+                  const long long ix = (long long)m * P->ldc + n + (long long)jn * (P->vpad - P->v);
+                  Th[ix] = T.h;
+                  Tl[ix] = T.l;
+                }
+                if (jn <= im) {
+                  const long long ix = (long long)n * P->ldc + m + (long long)im * (P->vpad - P->v);
+                  Th[ix] = T.h;
+                  Tl[ix] = T.l;
+                }
+                emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
+              }
             }
-            if (jn <= im) {
-              const long long ix = (long long)n * P->ldc + m + (long long)im * (P->vpad - P->v);
-              Th[ix] = T.h;
-              Tl[ix] = T.l;
-            }
-            emax = max(emax, (__float_as_uint(T.h) >> 23) & 0xFFu);
           }
         } else {
           double* C = (P->kind == PK_GAMMA || P->kind == PK_RAW) ? bs.gamma
