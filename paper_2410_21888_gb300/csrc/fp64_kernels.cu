@@ -382,7 +382,7 @@ __global__ void k_check_inputs(const FragDev* __restrict__ frags, Bases bs) {
   const double* B = bs.B + F.b_off;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nb; e += stride)
-    bad_nf |= !isfinite(B[e]);
+    bad_nf |= !finite_bits(B[e]);
   if (blockIdx.x == 0) {
     __shared__ double smax[256], smin[256];
     double mx = -INFINITY, mn = INFINITY;

@@ -16,6 +16,54 @@ enum : unsigned {
   ST_INTERNAL = 8u,   // a device-side index check failed (access skipped)
 };
 
+// FP64 inputs read on the integer pipes: this GPU's FP64 unit runs at a small fraction of
+// its FP32 and integer rates, and its conversions and comparisons would bound the
+// element-wise kernels that read B.
+#ifdef __CUDACC__
+// |x| as an integer key: non-negative doubles order like their bit patterns
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// x is neither Inf nor NaN
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu) != 0x7FFu;
+}
+// ilogb of a positive double given by its bits (exponent field; FP64 subnormals, far below
+// any input this library sees, take the FP64 route)
+__device__ __forceinline__ int ilogb_bits(unsigned long long b) {
+  const int e = (int)((b >> 52) & 0x7FFu);
+  return e != 0 ? e - 1023 : ilogb(__longlong_as_double((long long)b));
+}
+// h = (float)x and l = (float)(x - (double)h), both correctly rounded, from the bits of x:
+// the 53-bit significand rounded to 24 bits (to nearest, ties to even) gives h, and the
+// exact remainder, an integer below 2^29 in units of x's last bit, converted with
+// rounding and scaled by a power of two gives l.  Bit-identical to the two conversions
+// wherever h and any non-zero l are normal floats (|x| in [2^-74, 2^127)); other inputs,
+// far from anything this library sees, take the FP64 conversions.
+__device__ __forceinline__ void split_to_df(double x, float& h, float& l) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FFu);
+  if (e < 949 || e > 1149) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+    return;
+  }
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long r = m & ((1ull << 29) - 1);
+  unsigned long long mh = m >> 29;
+  if (r > (1ull << 28) || (r == (1ull << 28) && (mh & 1ull))) ++mh;
+  // fraction field mh - 2^23 added to the exponent field: a carry (mh = 2^24) raises it
+  h = __uint_as_float(sign + ((unsigned)(e - 1023 + 127) << 23) + (unsigned)(mh - (1ull << 23)));
+  const int d = (int)((long long)m - (long long)(mh << 29));   // |d| <= 2^28
+  // 2^(e - 1075) as two normal factors; x - h = 0 rounds to +0 whatever the sign of x
+  const int k = e - 1075, k1 = k / 2, k2 = k - k1;
+  const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
+  const float lv = (__int2float_rn(d) * s1) * s2;
+  l = d == 0 ? 0.0f : (sign ? -lv : lv);
+}
+#endif
+
 // Kinds of contraction problems handled by the grouped GEMM kernels.
 enum ProbKind : int {
   PK_V = 0,      // V_ij(a,b) = sum_Q B B over (i,a)x(j,b), upper triangle of tiles,

@@ -233,18 +233,19 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
   const SplitFragDev& F = f[find_sfd(f, nf, gr, 0)];
   const int r = (int)(gr - F.row_begin);
   const double* x = bs.B + F.b_off + (long long)r * F.X;
-  double mx = 0.0, ss = 0.0;
+  unsigned long long mx = 0;   // max |x| as bits
+  double ss = 0.0;
   for (int q = lane; q < F.X; q += 32) {
     const double xq = x[q];
-    mx = fmax(mx, fabs(xq));
+    mx = max(mx, abs_bits(xq));
     ss = fma(xq, xq, ss);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     ss += __shfl_xor_sync(0xffffffffu, ss, off);
   }
-  const int E = mx > 0.0 ? ilogb(mx) + 2 + Digit<F8>::HEAD : -1000;
+  const int E = mx > 0 ? ilogb_bits(mx) + 2 + Digit<F8>::HEAD : -1000;
   char* ws = (char*)bs.ws;
   const long long plane = (long long)F.o * F.v * F.xpad;
   DT* out = (DT*)(ws + F.bs1) + (long long)r * F.xpad;
@@ -256,9 +257,8 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
     dfl xs[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double xq = q0 + k < F.X ? x[q0 + k] : 0.0;
-      const float h = (float)xq;
-      const float l = (float)(xq - (double)h);
+      float h, l;
+      split_to_df(q0 + k < F.X ? x[q0 + k] : 0.0, h, l);
       xs[k] = {(h * s1) * s2, (l * s1) * s2};
     }
     put4<F8>(xs, sv, out + q0, plane);
@@ -278,7 +278,7 @@ k_slice_b1(const SplitFragDev* __restrict__ f, int nf, long long rows, int sv, B
 // bits combined by atomicMax (non-negative doubles order like their bit patterns).
 __global__ void __launch_bounds__(256)
 k_bcol_max(const SplitFragDev* __restrict__ f, int nf, Bases bs) {
-  __shared__ double red[8][32];
+  __shared__ unsigned long long red[8][32];   // |B| maxima as bits
   const long long gb = blockIdx.x;
   const SplitFragDev& F = f[find_sfd(f, nf, gb, 3)];
   const long long lb = gb - F.qblk_begin;
@@ -287,19 +287,17 @@ k_bcol_max(const SplitFragDev* __restrict__ f, int nf, Bases bs) {
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int Q = qb * 32 + lane;
   const int r0 = rc * 256, r1 = min(F.o * F.v, r0 + 256);
-  double mx = 0.0;
+  unsigned long long mx = 0;
   if (Q < F.X) {
     const double* x = bs.B + F.b_off + Q;
 #pragma unroll 8
-    for (int r = r0 + g; r < r1; r += 8) mx = fmax(mx, fabs(x[(long long)r * F.X]));
+    for (int r = r0 + g; r < r1; r += 8) mx = max(mx, abs_bits(x[(long long)r * F.X]));
   }
   red[g][lane] = mx;
   __syncthreads();
   if (g == 0) {
-    for (int k = 1; k < 8; ++k) mx = fmax(mx, red[k][lane]);
-    if (Q < F.X && mx > 0.0)
-      atomicMax((unsigned long long*)((char*)bs.ws + F.ecolm) + Q,
-                (unsigned long long)__double_as_longlong(mx));
+    for (int k = 1; k < 8; ++k) mx = max(mx, red[k][lane]);
+    if (Q < F.X && mx > 0) atomicMax((unsigned long long*)((char*)bs.ws + F.ecolm) + Q, mx);
   }
 }
 
@@ -338,8 +336,7 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
   const int qi = threadIdx.x >> 3, cg = threadIdx.x & 7;
   const int Q = tq * 32 + qi;
   if (Q >= F.X) return;
-  const double mq = __longlong_as_double((long long)cm[Q]);
-  const int E = mq > 0.0 ? ilogb(mq) + 2 + Digit<F8>::HEAD : -1000;
+  const int E = cm[Q] > 0 ? ilogb_bits(cm[Q]) + 2 + Digit<F8>::HEAD : -1000;
   if (tc == 0 && cg == 0) ec[Q] = E;
   float s1, s2;
   pow2_factors(Digit<F8>::LB - E, s1, s2);
@@ -350,9 +347,8 @@ k_slice_b2(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
     dfl xs[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double xq = tile[cl + k][qi];
-      const float h = (float)xq;
-      const float l = (float)(xq - (double)h);
+      float h, l;
+      split_to_df(tile[cl + k][qi], h, l);
       xs[k] = {(h * s1) * s2, (l * s1) * s2};
     }
     put4<F8>(xs, st, out + (long long)Q * F.ldd + c, plane);
