@@ -963,10 +963,9 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
                        ? n_tile : (slices <= 8 ? 64 : (slices <= 10 ? 48 : 32));
   } else {
     c.bk = bk == 16 ? 16 : 32;
-    // 64 columns by default: with 5 or 6 slices a stage is then small enough for three
-    // stages in shared memory, which outweighs the wider MMAs of 80- or 96-column tiles.
-    // (48 columns with 5 slices fit two accumulator sets in TMEM, 2 x 240 columns, but
-    // measured no faster: with 512-long chunks the drain is not what limits the kernel.)
+    // 64 columns when no width is asked for: with 5 or 6 slices a stage is then small
+    // enough for three stages in shared memory.  (The plan asks per launch: 48 for V,
+    // whose two accumulator sets then fit TMEM, 80 for Gamma, 64 for P_ab / P_ij.)
     const int widest = slices <= 5 ? 96 : (slices == 6 ? 80 : 64);
     c.n_tile_max = (n_tile == 48 || n_tile == 64 || n_tile == 80 || n_tile == 96)
                        ? std::min(n_tile, widest) : 64;
