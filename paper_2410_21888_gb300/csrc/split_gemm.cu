@@ -1,9 +1,9 @@
 // Split-precision tensor-core GEMM for sm_103a: TMA-fed, tcgen05.mma (kind::f16, BF16
 // in, FP32 TMEM accumulators), one persistent CTA per SM pulling tiles from a device
 // queue in LPT order.  Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues
-// the MMAs from one thread, warps 2..9 drain TMEM every 512-K chunk into double-float
-// registers and run the problem's epilogue (two accumulator sets alternate when both fit
-// the 512 TMEM columns).
+// the MMAs from one thread, warps 2..9 drain TMEM every K chunk (512 BF16 / 8192 FP8
+// elements) into double-float registers and run the problem's epilogue (two accumulator
+// sets alternate when both fit the 512 TMEM columns).
 //
 // Every mbarrier wait is bounded (globaltimer, 2 s): on expiry the CTA records
 // ST_TIMEOUT in the status word and stops all roles; the MMA issuer commits the MMAs it
