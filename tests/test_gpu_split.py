@@ -286,6 +286,25 @@ def test_gamma_rows_of_very_different_size():
     check_split(rimp2.energy_grad(B, eo, ev, precision="bf16"), ref)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_split_inputs_spanning_the_double_range(precision):
+    """The slicing kernels split FP64 inputs into double-floats with integer instructions
+    for |x| in [2^-74, 2^127) and fall back to FP64 conversions outside: B here mixes
+    ordinary entries with entries near 1e-30 and exact zeros (some aux columns and rows
+    tiny throughout, others mixed), and the results still match the oracle."""
+    rng = np.random.default_rng(29)
+    o, v, X = 6, 40, 90
+    eo = rng.uniform(-1.5, -0.3, o)
+    ev = rng.uniform(0.2, 3.0, v)
+    B = rng.normal(0.0, 0.05, (o, v, X))
+    B[:, :, 7] *= 1e-28            # an aux column far below 2^-74
+    B[2, 5, :] *= 1e-29            # a row far below it
+    B[1, 3, ::3] = 0.0             # exact zeros
+    B[4, :, 11] = rng.normal(0.0, 1e-24, v)
+    ref = oracle.fragment(B, eo, ev)
+    check_split(rimp2.energy_grad(B, eo, ev, precision=precision), ref)
+
+
 @pytest.mark.parametrize("dims", [(4, 60, 4000), (8, 40, 2000)])
 @pytest.mark.parametrize("precision,sv,tol", [("bf16", 4, 2e-11), ("fp8", 8, 1e-12)])
 def test_diagonal_dominated_energy_has_no_one_signed_error(dims, precision, sv, tol):
