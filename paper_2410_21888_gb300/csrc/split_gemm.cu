@@ -1,9 +1,9 @@
 // Split-precision tensor-core GEMM for sm_103a: TMA-fed, tcgen05.mma (kind::f16, BF16
 // in, FP32 TMEM accumulators), one persistent CTA per SM pulling tiles from a device
 // queue in LPT order.  Roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues
-// the MMAs from one thread, warps 2..9 drain TMEM every K chunk (512 BF16 / 8192 FP8
-// elements) into double-float registers and run the problem's epilogue (two accumulator
-// sets alternate when both fit the 512 TMEM columns).
+// the MMAs from one thread, the 8 or 16 epilogue warps (warps 2..) drain TMEM every K
+// chunk (512 BF16 / 8192 FP8 elements) into double-float registers and run the problem's
+// epilogue (two accumulator sets alternate when both fit the 512 TMEM columns).
 //
 // Every mbarrier wait is bounded (globaltimer, 2 s): on expiry the CTA records
 // ST_TIMEOUT in the status word and stops all roles; the MMA issuer commits the MMAs it
@@ -200,16 +200,27 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr)
+               : "memory");
+  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Columns c .. c+NC-1 of this warp's 32 TMEM lanes (NC a multiple of 8), issued without
+// Columns c .. c+NC-1 of this warp's 32 TMEM lanes (NC a multiple of 4), issued without
 // waiting; the values are valid after tmem_wait_ld and tmem_hold.
 template <int NC>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]) {
 #pragma unroll
   for (int g = 0; g < NC / 8; ++g) tmem_ld8(taddr + (uint32_t)(g * 8), v + g * 8);
+  if constexpr (NC % 8 == 4) tmem_ld4(taddr + (uint32_t)(NC - 4), v + NC - 4);
 }
 
 // Ties the registers of an asynchronous TMEM load to the point after tcgen05.wait::ld, so
@@ -220,6 +231,8 @@ __device__ __forceinline__ void tmem_hold(float (&v)[NC]) {
   for (int g = 0; g < NC / 8; ++g)
     asm volatile("" : "+f"(v[g * 8 + 0]), "+f"(v[g * 8 + 1]), "+f"(v[g * 8 + 2]), "+f"(v[g * 8 + 3]),
                  "+f"(v[g * 8 + 4]), "+f"(v[g * 8 + 5]), "+f"(v[g * 8 + 6]), "+f"(v[g * 8 + 7]));
+  if constexpr (NC % 8 == 4)
+    asm volatile("" : "+f"(v[NC - 4]), "+f"(v[NC - 3]), "+f"(v[NC - 2]), "+f"(v[NC - 1]));
 }
 
 // UMMA shared-memory descriptor of a K-major operand with ROWB-byte rows (64 or 32)
@@ -489,11 +502,14 @@ __device__ __forceinline__ void tma_operand(uint32_t dst, const CUtensorMap* tm,
 // F8 = false: BF16 digits (9 bits each, kind::f16); true: FP8 e4m3 digits (5 bits each,
 // kind::f8f6f4).  Both consume 32 bytes of K per MMA, so the tile geometry in bytes is
 // the same: ROWB bytes of K per row and pipeline stage.
-template <int NT, int ROWB, bool F8>
-__global__ void __launch_bounds__(SG_THREADS, 1)
+template <int NT, int ROWB, bool F8, int EPI>
+__global__ void __launch_bounds__((2 + EPI) * 32, 1)
 k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ begins, int nprobs,
              long long total, Bases bs, unsigned* __restrict__ counter, int slices, int stages) {
-  constexpr int NC = NT / 2;                 // columns per epilogue thread
+  constexpr int NC = NT / (EPI / 4);         // columns per epilogue thread
+  // two register buffers in the drain where the registers allow it (168 a thread with
+  // 8 epilogue warps, 96 with 16)
+  constexpr bool kDoubleBuf = EPI == 8 ? NC <= 24 : NC <= 12;
   constexpr uint32_t A_TILE = SG_BM * ROWB;  // bytes of one 128-row tile
   constexpr uint32_t B_TILE = NT * ROWB;
   constexpr int BKE = F8 ? ROWB : ROWB / 2;  // K elements per stage
@@ -521,7 +537,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
   // V epilogue: per epilogue warp, its NC columns' denominator terms and exponents, loaded
   // at the start of a tile (while the first chunk's MMAs run) instead of in the element loop
   float2* stage_dn = (float2*)(smem + (size_t)stages * stage_bytes + 256);
-  int* stage_eb = (int*)(stage_dn + SG_EPI_WARPS * NC);
+  int* stage_eb = (int*)(stage_dn + EPI * NC);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -531,11 +547,11 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(tmem_full + s, 1);
-      mbar_init(tmem_empty + s, SG_EPI_WARPS);
+      mbar_init(tmem_empty + s, EPI);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(tile_full + s, 1);
-      mbar_init(tile_empty + s, 1 + SG_EPI_WARPS);
+      mbar_init(tile_empty + s, 1 + EPI);
     }
     mbar_init(mma_drain, 1);
     *abort_flag = 0;
@@ -693,9 +709,9 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int ew = warp - 2;                   // 0..7
+    const int ew = warp - 2;                   // 0 .. EPI - 1
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
-    const int c0 = (ew >> 2) * NC;             // first column of this thread
+    const int c0 = (ew >> 2) * NC;             // first column of this thread (group ew / 4)
     const int row = quad * 32 + lane;          // row within the tile
     const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
     uint32_t cc = 0;
@@ -772,7 +788,7 @@ k_split_gemm(const SplitProb* __restrict__ probs, const long long* __restrict__ 
           __syncwarp();
           if (lane == 0) mbar_arrive(tmem_empty + set);
         };
-        if constexpr (NC <= 24) {
+        if constexpr (kDoubleBuf) {
           float va[NC], vb[NC];
           tmem_ld_cols<NC>(set_addr + (uint32_t)((slices - 1) * NT + c0), va);
           for (int l = slices - 1; l >= 0; l -= 2) {
@@ -972,23 +988,34 @@ SplitLaunch split_launch_config(int slices, int bk, int n_tile, bool fp8) {
   }
   const size_t rowb = fp8 ? 64 : (size_t)c.bk * 2;
   const size_t stage = (size_t)slices * (SG_BM + c.n_tile_max) * rowb;
-  // the V epilogue's staging area: per epilogue warp, n_tile / 2 columns x 12 bytes
-  const size_t stage_area = (size_t)SG_EPI_WARPS * (c.n_tile_max / 2) * 12;
+  // the V epilogue's staging area: per epilogue warp, its columns x 12 bytes
+  // (8 warps x n_tile / 2 columns, or 16 x n_tile / 4)
+  const size_t stage_area = (size_t)4 * c.n_tile_max * 12;
   const size_t budget = 227 * 1024 - 1024 - 256 - stage_area;
   int st = (int)(budget / stage);
   if (st > 8) st = 8;
   if (st < 1) st = 1;
   c.stages = st;
   c.smem = 1024 + (size_t)st * stage + 256 + stage_area;
+  c.epi_warps = 8;
   return c;
 }
 
+// 16 epilogue warps are built for the 32-wide K stages only (the shapes small fragments
+// use); other shapes run with 8
 template <int NT, int ROWB, bool F8>
 static cudaError_t launch_nt(const SplitProb* d_probs, const long long* d_begins, int nprobs,
                              long long total, Bases bs, unsigned* counter, const SplitLaunch& cfg,
                              int grid, cudaStream_t s) {
-  k_split_gemm<NT, ROWB, F8><<<grid, SG_THREADS, cfg.smem, s>>>(d_probs, d_begins, nprobs, total,
-                                                               bs, counter, cfg.slices, cfg.stages);
+  if constexpr (ROWB == 64) {
+    if (cfg.epi_warps == 16) {
+      k_split_gemm<NT, ROWB, F8, 16><<<grid, (2 + 16) * 32, cfg.smem, s>>>(
+          d_probs, d_begins, nprobs, total, bs, counter, cfg.slices, cfg.stages);
+      return cudaGetLastError();
+    }
+  }
+  k_split_gemm<NT, ROWB, F8, 8><<<grid, (2 + 8) * 32, cfg.smem, s>>>(
+      d_probs, d_begins, nprobs, total, bs, counter, cfg.slices, cfg.stages);
   return cudaGetLastError();
 }
 
@@ -996,15 +1023,18 @@ static cudaError_t launch_nt(const SplitProb* d_probs, const long long* d_begins
 cudaError_t split_gemm_prepare() {
   const int bytes = 227 * 1024;
   cudaError_t e = cudaSuccess;
-#define RIMP2_PREP(NT, ROWB, F8)                                                            \
+#define RIMP2_PREP(NT, ROWB, F8, EPI)                                                       \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_split_gemm<NT, ROWB, F8>,                                     \
+    e = cudaFuncSetAttribute(k_split_gemm<NT, ROWB, F8, EPI>,                                \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  RIMP2_PREP(96, 64, false) RIMP2_PREP(80, 64, false) RIMP2_PREP(64, 64, false)
-  RIMP2_PREP(48, 64, false)
-  RIMP2_PREP(96, 32, false) RIMP2_PREP(80, 32, false) RIMP2_PREP(64, 32, false)
-  RIMP2_PREP(48, 32, false)
-  RIMP2_PREP(64, 64, true) RIMP2_PREP(48, 64, true) RIMP2_PREP(32, 64, true)
+  RIMP2_PREP(96, 64, false, 8) RIMP2_PREP(80, 64, false, 8) RIMP2_PREP(64, 64, false, 8)
+  RIMP2_PREP(48, 64, false, 8)
+  RIMP2_PREP(96, 32, false, 8) RIMP2_PREP(80, 32, false, 8) RIMP2_PREP(64, 32, false, 8)
+  RIMP2_PREP(48, 32, false, 8)
+  RIMP2_PREP(64, 64, true, 8) RIMP2_PREP(48, 64, true, 8) RIMP2_PREP(32, 64, true, 8)
+  RIMP2_PREP(96, 64, false, 16) RIMP2_PREP(80, 64, false, 16) RIMP2_PREP(64, 64, false, 16)
+  RIMP2_PREP(48, 64, false, 16)
+  RIMP2_PREP(64, 64, true, 16) RIMP2_PREP(48, 64, true, 16) RIMP2_PREP(32, 64, true, 16)
 #undef RIMP2_PREP
   return e;
 }

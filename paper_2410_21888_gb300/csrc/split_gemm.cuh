@@ -36,8 +36,9 @@ constexpr int SG_LB_FP8 = 5, SG_CHUNK_K_FP8 = 8192, SG_HEAD_FP8 = 0;
 // K per pipeline stage: 32 (64-byte rows, 64B swizzle) or 16 (32-byte rows, 32B swizzle);
 // the smaller stage fits twice as many stages in shared memory
 constexpr int SG_MAX_SLICES = 16;   // FP8; BF16 stops at 8
-constexpr int SG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int SG_EPI_WARPS = 8;
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: 8 or 16 per launch (SplitLaunch::
+// epi_warps), each of the four TMEM lane quadrants served by 2 or 4 warps that split the
+// tile's columns between them
 
 // TMA coordinate modes of one operand
 enum : int {
@@ -85,6 +86,7 @@ struct SplitLaunch {
   int n_tile_max; // widest n_tile of the launch (smem layout)
   int stages;     // pipeline depth
   size_t smem;    // dynamic shared memory bytes
+  int epi_warps;  // epilogue warps: 8, or 16 (more warps for a tile's drain and epilogue)
 };
 
 // n_tile: columns per level accumulator (0: widest that fits 512 TMEM columns; else 64,

@@ -939,6 +939,15 @@ int split_build_wave(SplitPlan& sp, const rimp2_frag* frags, const std::vector<i
         P.ntiles = (long long)P.tiles_m * P.tiles_n * P.ksplit;
       }
     }
+  // Sixteen epilogue warps when every fragment's aux dimension is short: V's tiles then
+  // have little K for their MMAs to hide the T = V/D epilogue behind, which more warps
+  // share (MBE3 stated batch: dimer level 86.1 -> 79.3 ms); with naux ~1500 the extra
+  // warps cost V's MMA issuer a little (41.6 -> 42.2 ms at nocc=100 nvir=500).
+  {
+    int max_x = 0;
+    for (const auto& s : w.sfd) max_x = std::max(max_x, s.X);
+    w.epi_warps = max_x <= 1024 ? 16 : 8;
+  }
   total_pairs = pairs;
   w.rows = rows;
   w.b2_tiles = b2t;
@@ -1020,9 +1029,11 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   }
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_v > 0) {
+    SplitLaunch cfg = sp.cfg_v;
+    cfg.epi_warps = w.epi_warps;
     e = launch_split_gemm((const SplitProb*)(dblk + w.off_pv), (const long long*)(dblk + w.off_bv),
                           (int)w.probs_v.size(), w.tiles_v, bs,
-                          ctr + 0, sp.cfg_v, sp.grid, s);
+                          ctr + 0, cfg, sp.grid, s);
     ++nl;
   }
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
@@ -1036,16 +1047,20 @@ int split_enqueue_wave(SplitPlan& sp, SplitWave& w, char* dblk, const FragDev* d
   if (e == cudaSuccess) { e = launch_zero_p(dfd, nf, bs, s); ++nl; }
   if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_c > 0) {
+    SplitLaunch cfg = sp.cfg_t;
+    cfg.epi_warps = w.epi_warps;
     e = launch_split_gemm((const SplitProb*)(dblk + w.off_pc), (const long long*)(dblk + w.off_bc),
                           (int)w.probs_c.size(), w.tiles_c, bs,
-                          ctr + 1, sp.cfg_t, sp.grid, s);
+                          ctr + 1, cfg, sp.grid, s);
     ++nl;
   }
   if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
   if (e == cudaSuccess && w.tiles_g > 0) {
+    SplitLaunch cfg = sp.cfg_g;
+    cfg.epi_warps = w.epi_warps;
     e = launch_split_gemm((const SplitProb*)(dblk + w.off_pg), (const long long*)(dblk + w.off_bg),
                           (int)w.probs_g.size(), w.tiles_g, bs,
-                          ctr + 2, sp.cfg_g, sp.grid, s);
+                          ctr + 2, cfg, sp.grid, s);
     ++nl;
   }
   if (ev) cudaEventRecordWithFlags(ev[5], s, cudaEventRecordExternal);

@@ -67,6 +67,7 @@ struct SplitWave {
   std::vector<SplitProb> probs_v, probs_c, probs_g;   // V; P_ab / P_ij; Gamma
   long long tiles_v = 0, tiles_c = 0, tiles_g = 0, rows = 0, b2_tiles = 0, qblks = 0;
   bool want_gamma = false;
+  int epi_warps = 8;   // epilogue warps of the wave's contraction launches (see build)
   double mma_v = 0, mma_c = 0, mma_g = 0;   // tensor-core FLOPs issued per launch
   size_t off_sfd = 0, off_pv = 0, off_pc = 0, off_pg = 0;  // byte offsets in the device block
   size_t off_bv = 0, off_bc = 0, off_bg = 0;  // the problems' tile_begin values (int64 each)
