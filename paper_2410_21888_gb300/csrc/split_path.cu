@@ -194,7 +194,9 @@ __device__ __forceinline__ f2x digit_step2(f2x& xh, f2x& xl) {
 // Digits of four consecutive elements (double-floats x[k] already scaled to the slice
 // frame), one packed store per slice plane; the digit steps run on element pairs.  NS > 0:
 // the plane count is NS, known at compile time (the loop unrolls; st is not read).
-template <bool F8, int NS = 0>
+// STREAM: the stores carry the evict-first hint (the amplitude kernel's digit planes are
+// far larger than L2 and are read back by later launches only).
+template <bool F8, int NS = 0, bool STREAM = false>
 __device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* out,
                                      long long plane) {
   constexpr int LB = Digit<F8>::LB;
@@ -205,7 +207,8 @@ __device__ __forceinline__ void put4(dfl x[4], int st, typename Digit<F8>::T* ou
     float d0, d1, d2, d3;
     f2_unpack(digit_step2<LB>(h01, l01), d0, d1);
     f2_unpack(digit_step2<LB>(h23, l23), d2, d3);
-    *(PT*)(out + p * plane) = Pack4<F8>::pack(d0, d1, d2, d3);
+    if constexpr (STREAM) __stcs((PT*)(out + p * plane), Pack4<F8>::pack(d0, d1, d2, d3));
+    else *(PT*)(out + p * plane) = Pack4<F8>::pack(d0, d1, d2, d3);
   };
   if constexpr (NS > 0) {
 #pragma unroll
@@ -476,11 +479,11 @@ k_amp_split(const SplitFragDev* __restrict__ f, int nf, int st, Bases bs) {
       tt[k] = {(tt[k].h * s1tt) * s2tt, (tt[k].l * s1tt) * s2tt};
     }
     if (ns) {
-      put4<F8, NS>(t, stt, ts + o_, plane);
-      put4<F8, NS>(tt, st, tts + o_, plane);
+      put4<F8, NS, true>(t, stt, ts + o_, plane);
+      put4<F8, NS, true>(tt, st, tts + o_, plane);
     } else {
-      put4<F8>(t, stt, ts + o_, plane);
-      put4<F8>(tt, st, tts + o_, plane);
+      put4<F8, 0, true>(t, stt, ts + o_, plane);
+      put4<F8, 0, true>(tt, st, tts + o_, plane);
     }
   };
 
